@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Throughput of the strong-field QED Monte Carlo substep on GB300.
+
+Workload (the precision-study case): 10^8 particles, 5e7 electrons and 5e7
+photons drawn from the paper's §4 benchmark distribution (E, B components
+uniform in +-E_s/100, p components uniform in +-1 GeV/c, optical depth
+exponential), FP32 structure of arrays with a Kahan word for the optical depth,
+tables of 256 points and 256x256 generated in FP64 on the GPU, dt = 10 hbar/(m_e c^2).
+One step = one qed_substep call: evolution of all three species in one batched
+launch, pair production, photon emission, secondaries appended.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QED substep particle-steps/s on 1 GB300 (FP32 table & MLP vs FP64 table), % HBM peak"
+UNIT = "particle-steps/s"
+WORKLOAD = "precision study: 1e8 mixed particles (5e7 e-, 5e7 photons), FP32 SoA + Kahan tau, 256/256x256 tables"
+N_PER_SPECIES = 50_000_000
+DT = 10.0
+SEED = 20211001
+BYTES_F32 = 52  # algorithmic bytes per evolved particle: p, E, B, tau, tau_c read (44) + tau, tau_c written (8)
+BYTES_F64 = 88  # p, E, B, tau read (80) + tau written (8)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=N_PER_SPECIES, help="particles per species (electrons, photons)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(kernel_src: str):
+    """DRAM bytes per particle of the evolution kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "evolve_kernel_fp32_traffic.txt")
+    try:
+        rec = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return float(rec["dram_bytes_per_particle"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------------------
+def make_species(api, workloads, prec, n, extra, seed, rank):
+    import torch
+    dt = torch.float32 if prec == api.QED_F32 else torch.float64
+    bufs = {}
+    for k, s, off in (("electrons", 1, 0), ("photons", 2, 2 * 10 ** 12)):
+        b = api.SpeciesBuffers(n + extra, prec)
+        d = workloads.paper_benchmark_torch(n, seed + 7919 * rank + s, off + rank * 10 ** 10, dtype=dt)
+        for c, v in d.items():
+            b.arrays[c][:n].copy_(v)
+        del d
+        b.count.fill_(n)
+        bufs[k] = b
+    bufs["positrons"] = api.SpeciesBuffers(extra, prec)
+    fire = [api.FireBuffers(bufs[k].capacity) for k in ("electrons", "positrons", "photons")]
+    return bufs, fire
+
+
+def counts(bufs):
+    return sum(int(bufs[k].count.item()) for k in ("electrons", "positrons", "photons"))
+
+
+def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True):
+    import torch
+    stats = api.Stats()
+    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats)
+    for s in range(warmup):
+        call(step0 + s)
+    torch.cuda.synchronize()
+    n_before = counts(bufs)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:  # materialise the events
+        a.record(stream), b.record(stream)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(steps):
+        if evolve_events:
+            call.opts.evolve_begin = evs[s][0].cuda_event
+            call.opts.evolve_end = evs[s][1].cuda_event
+        call(step0 + warmup + s)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = t0.elapsed_time(t1)
+    ev_ms = [a.elapsed_time(b) for a, b in evs] if evolve_events else []
+    n_after = counts(bufs)
+    return dict(ms=ms, n_before=n_before, n_after=n_after, evolve_ms=ev_ms, stats=stats.as_dict())
+
+
+def e2e_leg(api, t, bufs, fire, steps, ws):
+    """Same metric through the C ABI with host buffers: every step copies the
+    inputs host -> device from pinned memory, runs the substep, and copies the
+    updated optical depths and momenta back."""
+    import torch
+    names_in = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz", "tau", "tau_c")
+    names_out = ("px", "py", "pz", "tau", "tau_c")
+    host = {}
+    for k in ("electrons", "photons"):
+        n = int(bufs[k].count.item())
+        host[k] = {c: bufs[k].arrays[c][:n].cpu().pin_memory() for c in names_in}
+    out = {k: {c: torch.empty_like(host[k][c]).pin_memory() for c in names_out} for k in host}
+    counts_h = torch.zeros(3, dtype=torch.int64).pin_memory()
+    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED)
+    stream = torch.cuda.current_stream()
+    bi = sum(v.numel() * v.element_size() for d in host.values() for v in d.values())
+    bo = sum(v.numel() * v.element_size() for d in out.values() for v in d.values()) + counts_h.numel() * 8
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_step = counts(bufs)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(steps):
+        for k in host:
+            n = host[k]["px"].numel()
+            for c in names_in:
+                bufs[k].arrays[c][:n].copy_(host[k][c], non_blocking=True)
+            bufs[k].count.fill_(n)
+        bufs["positrons"].count.zero_()
+        call(10_000 + s)
+        for k in host:
+            n = host[k]["px"].numel()
+            for c in names_out:
+                out[k][c].copy_(bufs[k].arrays[c][:n], non_blocking=True)
+        counts_h[0:1].copy_(bufs["electrons"].count, non_blocking=True)
+        counts_h[1:2].copy_(bufs["positrons"].count, non_blocking=True)
+        counts_h[2:3].copy_(bufs["photons"].count, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = t0.elapsed_time(t1)
+    del host, out
+    return ms, n_step, bi, bo
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle
+    from paper_2110_00256_gb300 import workloads
+    ot = oracle.tables()
+    m = 250_000
+    sp = {"electrons": workloads.paper_benchmark(m, 11, 0), "photons": workloads.paper_benchmark(m, 12, 10 ** 12),
+          "positrons": workloads.paper_benchmark(0, 13, 2 * 10 ** 12)}
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        out = oracle.substep(ot, sp, dt=DT, seed=SEED, step=steps)
+        sp = {k: {c: out[k][c] for c in sp[k]} for k in sp}
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 2 * m * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{2 * m} particles (paper §4 distribution, 256/256x256 FP64 oracle tables), {steps} substeps, "
+                      f"{el:.1f} s wall; evolution OpenMP-parallel over particles, events serial"}
+
+
+def gpu_main(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2110_00256_gb300 import api, build, workloads
+    if rank == 0 or ws == 1:
+        build.build()
+    barrier(ws)
+
+    t_gen0 = time.perf_counter()
+    tabs = api.qed_tables_generate(api.table_params())
+    gen_ms = (time.perf_counter() - t_gen0) * 1e3
+
+    n = args.n
+    extra = max(4_000_000, n // 25)
+    bufs, fire = make_species(api, workloads, api.QED_F32, n, extra, SEED, rank)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    r = time_substep(api, tabs, bufs, fire, args.steps, args.warmup, ws)
+    clk = clocks.stop()
+
+    ms_max = max_over_ranks(ws, r["ms"])
+    total = sum_over_ranks(ws, r["n_before"] * args.steps)
+    value = total / (ms_max * 1e-3)
+    ev = r["evolve_ms"]
+    ev_mean = sum(ev) / len(ev)
+    hbm, which = peaks()
+    ach = BYTES_F32 * r["n_before"] / (ev_mean * 1e-3) / 1e9
+    traffic_bpp = traffic_record(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "evolve.cu"))
+    roofline = {"bound": "hbm", "kernel": "evolve_kernel<float,4>", "achieved": round(ach, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_kind": which,
+                "traffic": (traffic_bpp * r["n_before"]) if traffic_bpp else None,
+                "algorithmic_bytes": BYTES_F32 * r["n_before"], "evolve_ms": round(ev_mean, 4),
+                "frac_of_8TBs": round(ach / 8000.0, 4)}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "particles": 2 * n, "electrons": n, "photons": n, "dt": DT,
+                         "tables": "256 / 256x256, FP64 generated on the GPU, FP32 copies", "seed": SEED,
+                         "l2": "inputs (%.1f GB) larger than L2, no flush" % (2 * n * 48 / 1e9),
+                         "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                         "table_generation_ms": round(gen_ms, 1)},
+              "roofline": roofline,
+              "gpu_launches": 6 * args.steps,
+              "events_per_step": {k: v / (args.warmup + args.steps) for k, v in r["stats"].items() if v}}
+    if clk:
+        result["clocks"] = clk
+
+    # FP64 table path beside it (same workload, FP64 SoA)
+    if not args.no_fp64:
+        del bufs, fire
+        torch.cuda.empty_cache()
+        b64, f64 = make_species(api, workloads, api.QED_F64, n, extra, SEED, rank)
+        r64 = time_substep(api, tabs, b64, f64, max(3, args.steps // 4), 2, ws)
+        ms64 = max_over_ranks(ws, r64["ms"])
+        tot64 = sum_over_ranks(ws, r64["n_before"] * max(3, args.steps // 4))
+        ev64 = sum(r64["evolve_ms"]) / len(r64["evolve_ms"])
+        ach64 = BYTES_F64 * r64["n_before"] / (ev64 * 1e-3) / 1e9
+        result["paths"] = {"fp64_table": {"value": tot64 / (ms64 * 1e-3), "unit": UNIT,
+                                          "ms_per_step": ms64 / max(3, args.steps // 4),
+                                          "evolve_ms": round(ev64, 4), "hbm_gbs": round(ach64, 1),
+                                          "hbm_frac": round(ach64 / hbm, 4)}}
+        bufs, fire = b64, f64
+        del b64, f64
+        torch.cuda.empty_cache()
+        bufs, fire = make_species(api, workloads, api.QED_F32, n, extra, SEED, rank)
+
+    if not args.no_e2e:
+        k = min(args.steps, 5)
+        ms, n_step, bi, bo = e2e_leg(api, tabs, bufs, fire, k, ws)
+        ms = max_over_ranks(ws, ms)
+        result["e2e"] = {"value": sum_over_ranks(ws, n_step * k) / (ms * 1e-3), "unit": UNIT,
+                         "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": k,
+                         "ms_per_step": ms / k}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------
+# reference leg: the oracle, timed on the host cores
+# ----------------------------------------------------------------------------------------
+def reference_main(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2110_00256_gb300 import workloads
+    ot = oracle.tables()
+    m = 100_000  # particles per species per step: the bounded sample
+    sp = {"electrons": workloads.paper_benchmark(m, 11, 0), "photons": workloads.paper_benchmark(m, 12, 10 ** 12),
+          "positrons": workloads.paper_benchmark(0, 13, 2 * 10 ** 12)}
+    for s in range(args.warmup):
+        out = oracle.substep(ot, sp, dt=DT, seed=SEED, step=s)
+        sp = {k: {c: out[k][c] for c in sp[k]} for k in sp}
+    n_proc = 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        n_proc += sum(len(sp[k]["px"]) for k in sp)
+        out = oracle.substep(ot, sp, dt=DT, seed=SEED, step=args.warmup + s)
+        sp = {k: {c: out[k][c] for c in sp[k]} for k in sp}
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = n_proc / el
+    sample = f"{2 * m} particles per step of the same distribution (FP64 oracle, 256/256x256 oracle tables)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference_main(a)
+    else:
+        gpu_main(a)

@@ -1,0 +1,218 @@
+/*
+ * qed.h -- C ABI of libqed, a GB300 (sm_103a) implementation of the per-particle
+ * strong-field QED Monte Carlo substep of PICSAR-QED (Fedeli et al., arXiv
+ * 2110.00256): optical-depth evolution, quantum-synchrotron (QS) photon emission
+ * and nonlinear Breit-Wheeler (BW) pair production.
+ *
+ * Units (one normalised system): momentum in m_e c; E in the Schwinger field
+ * E_s = m_e^2 c^3 / (q_e hbar) (§2); B in E_s / c; time in hbar / (m_e c^2).
+ * Then the rates are dN/dt = (2/3) alpha G(chi) / gamma for QS (Eq.
+ * (qs_total_cross)) and dN/dt = alpha chi_g T(chi_g) / gamma_g for BW (Eq.
+ * (bw_cross_tot)), alpha = 7.2973525693e-3.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a qed_status; QED_OK = 0.  On error nothing has been
+ *    enqueued and qed_last_error_message() (thread-local) says why.  No C++
+ *    exception crosses this boundary.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take a stream only enqueue work and return without
+ *    synchronising, unless stated otherwise; they never allocate device memory
+ *    and are safe to capture in a CUDA graph.
+ *  - Particle buffers are owned by the caller (device memory, structure of
+ *    arrays).  Tables are owned by the library through an opaque handle.
+ *  - A pointer documented as "device" must be device memory of the current
+ *    device; "host" means ordinary host memory.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qed_status;
+enum {
+    QED_OK = 0,
+    QED_ERR_INVALID_ARG = 1, /* a NULL, misaligned or out-of-range argument            */
+    QED_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error)  */
+    QED_ERR_CAPACITY = 3,    /* reported through QED_STAT_DROPPED_CAPACITY, see below    */
+    QED_ERR_NUMERIC = 4,     /* non-finite input seen (also counted in the stats)         */
+    QED_ERR_TIMEOUT = 5,     /* a bounded wait gave up                                    */
+    QED_ERR_IO = 6,          /* file could not be read/written or has a bad header       */
+    QED_ERR_UNSUPPORTED = 7  /* parameter combination not built into this library         */
+};
+
+typedef enum { QED_F32 = 0, QED_F64 = 1 } qed_precision;
+typedef enum { QED_PROC_QS = 0, QED_PROC_BW = 1 } qed_process;
+
+/* Axis of one process's tables (§3.1, §3.2).  chi grid: n_chi points
+ * log-spaced on [chi_min, chi_max], both ends included.  xi grid of the 2-D
+ * table: QS, n_xi points log-spaced on [xi_min, 1]; BW, n_xi points linearly
+ * spaced on [0, 1/2] (xi_min unused).  2 <= n_chi, n_xi <= QED_MAX_TABLE_N. */
+typedef struct {
+    double chi_min, chi_max;
+    int32_t n_chi, n_xi;
+    double xi_min;
+} qed_table_axis;
+
+typedef struct {
+    qed_table_axis qs, bw;
+} qed_table_params;
+
+#define QED_MAX_TABLE_N 1024
+
+typedef struct qed_tables qed_tables; /* opaque, library-owned */
+
+/* One species, structure of arrays, caller-owned device memory.
+ * px..bz, tau, weight: element type float (QED_F32) or double (QED_F64),
+ * `capacity` elements each.  tau_c: FP32 only, the Kahan compensation of tau
+ * (the optical depth is tau - tau_c); ignored (may be NULL) for QED_F64.
+ * id: per-particle 64-bit identifier, the counter of every random draw.
+ * d_count: device int64, number of live particles (read by every kernel, grown
+ * by the event kernels that append to this species).
+ * Vector loads are used when every array is 16-byte aligned. */
+typedef struct {
+    void *px, *py, *pz;
+    void *ex, *ey, *ez;
+    void *bx, *by, *bz;
+    void *tau, *tau_c, *weight;
+    uint64_t *id;
+    int64_t capacity;
+    int64_t *d_count;
+} qed_species;
+
+/* Device list of the particles whose optical depth went negative in the
+ * last evolution: index into the species, and the chi it had (FP64). */
+typedef struct {
+    int64_t *idx;     /* device, `capacity` entries                    */
+    double *chi;      /* device, `capacity` entries                    */
+    int64_t *d_count; /* device int64, number of entries               */
+    int64_t capacity; /* >= the species capacity, or entries are lost  */
+} qed_fire_list;
+
+/* Device counters, accumulated (never reset by the library).  int64 each. */
+enum {
+    QED_STAT_QS_EVENTS = 0,          /* photon emissions executed                         */
+    QED_STAT_BW_EVENTS = 1,          /* photon decays executed (pair or below threshold)  */
+    QED_STAT_PHOTONS_KEPT = 2,       /* photons appended                                  */
+    QED_STAT_PHOTONS_DISCARDED = 3,  /* photons below the keep threshold (§5)             */
+    QED_STAT_PAIRS = 4,              /* e-/e+ pairs appended                              */
+    QED_STAT_BW_NO_PAIR = 5,         /* decays of photons with gamma_g <= 2 (no pair)     */
+    QED_STAT_DROPPED_CAPACITY = 6,   /* events not executed: a destination was full       */
+    QED_STAT_NONFINITE = 7,          /* particles with non-finite chi or optical depth    */
+    QED_STAT_FIRE_OVERFLOW = 8,      /* firing particles beyond the fire-list capacity    */
+    QED_STAT_COUNT = 9
+};
+
+typedef struct {
+    double photon_threshold; /* photons with gamma_g below this are not kept, the emitter
+                                still recoils (§5); 0 keeps every photon                     */
+    int32_t sampler;         /* 0: 2-D inverse-CDF tables; 1: MLP surrogate (qed_mlp)         */
+    const void *mlp;         /* qed_mlp* when sampler == 1                                    */
+    int64_t *d_stats;        /* device int64[QED_STAT_COUNT], or NULL                         */
+    void *evolve_begin;      /* optional cudaEvent_t recorded on the stream right before the
+                                evolution launch of qed_substep (timing); NULL: none          */
+    void *evolve_end;        /* optional cudaEvent_t recorded right after that launch         */
+} qed_substep_opts;
+
+/* ------------------------------------------------------------------------- */
+/* library                                                                   */
+/* ------------------------------------------------------------------------- */
+const char *qed_last_error_message(void);
+const char *qed_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* tables (§3.1, §3.2; generation §3 and §5)                                  */
+/* ------------------------------------------------------------------------- */
+/* Build the four tables in FP64 on the GPU (ln G, ln P for QS; ln T, P for BW)
+ * by quadrature of the modified Bessel functions (Eqs. (t_func_0),
+ * (bw_prob_dist), (qs_g_func), (qs_prob_dist)), and keep FP32 copies rounded
+ * to nearest (§3.3: tables may be computed in FP64 and kept in FP32).  Synchronises
+ * `stream` before returning.  *out receives a new handle. */
+qed_status qed_tables_generate(const qed_table_params *params, qed_tables **out, void *stream);
+
+/* Make tables from host arrays (FP64, row-major [n_chi][n_xi]): qs_lnG[qs.n_chi],
+ * qs_lnP[qs.n_chi * qs.n_xi], bw_lnT[bw.n_chi], bw_P[bw.n_chi * bw.n_xi].  The
+ * arrays are copied; the caller keeps ownership.  Synchronises `stream`. */
+qed_status qed_tables_create(const qed_table_params *params, const double *qs_lnG,
+                             const double *qs_lnP, const double *bw_lnT, const double *bw_P,
+                             qed_tables **out, void *stream);
+
+/* Copy the FP64 tables into host arrays laid out as for qed_tables_create (any
+ * pointer may be NULL to skip that table).  Synchronous. */
+qed_status qed_tables_copy_to_host(const qed_tables *t, double *qs_lnG, double *qs_lnP,
+                                   double *bw_lnT, double *bw_P);
+
+qed_status qed_tables_get_params(const qed_tables *t, qed_table_params *out);
+
+/* Binary file: magic, version, params, the four FP64 arrays, a 64-bit
+ * checksum.  Load verifies all of them and returns QED_ERR_IO on mismatch. */
+qed_status qed_tables_save(const qed_tables *t, const char *path);
+qed_status qed_tables_load(const char *path, qed_tables **out, void *stream);
+
+qed_status qed_tables_destroy(qed_tables *t);
+
+/* ------------------------------------------------------------------------- */
+/* optical depth (§3)                                                         */
+/* ------------------------------------------------------------------------- */
+/* tau = -ln U for particles [0, *d_count), U the 53-bit Philox4x32-10 uniform of
+ * (key = seed, counter = (id, step, 2)), computed in FP64; for QED_F32 tau_c
+ * receives the rounding residual so that tau - tau_c keeps the FP64 value. */
+qed_status qed_init_optical_depth(const qed_species *sp, qed_precision prec, uint64_t seed,
+                                  int64_t step, void *stream);
+
+/* Evolve the optical depth of every particle of `sp` (§3, Fig. scheme):
+ * chi from its definition in §2 (lepton or photon), rate from the 1-D table (log-log interpolation of
+ * §3.1/§3.2; QS clamps outside the table, BW uses the asymptotes of Eq.
+ * (t_func)), tau -= rate * dt (FP32: Kahan-compensated with tau_c).  Particles
+ * whose optical depth becomes negative are appended to `fire` (index and chi);
+ * fire->d_count is reset by this call.  `stats` may be NULL. */
+qed_status qed_evolve_optical_depth(const qed_tables *t, qed_process proc, const qed_species *sp,
+                                    double dt, qed_precision prec, const qed_fire_list *fire,
+                                    int64_t *d_stats, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* events                                                                    */
+/* ------------------------------------------------------------------------- */
+/* Photon emission for the firing leptons in `fire` (§2.2, §3.2): xi by
+ * inverse-CDF sampling of the 2-D table with U from (seed, (id, step, 0)),
+ * gamma_g = (gamma - 1) xi along p; the lepton keeps its direction with
+ * gamma' = gamma - gamma_g; its optical depth is reset to -ln U(id, step, 1).
+ * The photon (id from (id, step, 3), tau from its own id and purpose 2, the
+ * parent's weight, E and B) is appended to `photons` if gamma_g >=
+ * opts->photon_threshold.  If `photons` is full the event is not executed (the
+ * lepton keeps tau < 0 and fires again next step) and
+ * QED_STAT_DROPPED_CAPACITY counts it. */
+qed_status qed_generate_photons(const qed_tables *t, const qed_species *leptons,
+                                const qed_species *photons, const qed_fire_list *fire,
+                                uint64_t seed, int64_t step, const qed_substep_opts *opts,
+                                qed_precision prec, void *stream);
+
+/* Pair production for the firing photons in `fire` (§2.1, §3.1): r from
+ * (seed, (id, step, 0)); r <= 1/2 samples the electron's xi, otherwise the
+ * positron's with r -> 1 - r; K_pm = (gamma_g - 2) xi_pm, both along the photon
+ * momentum.  The photon is removed (weight 0, tau = +inf).  gamma_g <= 2 makes
+ * no pair: the photon stays, tau reset from purpose 1.  Capacity as above (an
+ * event needs a slot in both lepton species). */
+qed_status qed_generate_pairs(const qed_tables *t, const qed_species *photons,
+                              const qed_species *electrons, const qed_species *positrons,
+                              const qed_fire_list *fire, uint64_t seed, int64_t step,
+                              const qed_substep_opts *opts, qed_precision prec, void *stream);
+
+/* The whole substep on three species: one batched evolution launch over
+ * electrons (QS), positrons (QS) and photons (BW), then pair production, then
+ * photon emission.  fire[0..2] are the firing lists of the three species in
+ * that order.  Products are appended after the live particles and are first
+ * evolved in the next call.  Graph-capturable. */
+qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
+                       const qed_species *positrons, const qed_species *photons, double dt,
+                       uint64_t seed, int64_t step, const qed_substep_opts *opts,
+                       qed_precision prec, const qed_fire_list *fire, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QED_H */

@@ -112,6 +112,9 @@ def lib():
             "oracle_bw_events": (None, [C.POINTER(Tables), _I64] + [_P] * 5 + [_U64, _I64]
                                  + [_P] * 11),
             "oracle_init_tau": (None, [_I64, _P, _U64, _I64, _P]),
+            "oracle_rates": (None, [C.c_int, C.POINTER(Tables), _I64, _P, _P, _P]),
+            "oracle_qs_table_cdf": (_D, [C.POINTER(Tables), _D, _D]),
+            "oracle_bw_table_cdf": (_D, [C.POINTER(Tables), _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -283,6 +286,22 @@ class OracleTables:
 
     def bw_T(self, chig):
         return lib().oracle_bw_T_table(C.byref(self.struct), chig)
+
+    def rates(self, proc, chi, energy):
+        """Vectorised rate lookup; energy is gamma (QS) or |p| (BW)."""
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        energy = np.ascontiguousarray(energy, dtype=np.float64)
+        out = np.zeros(chi.shape[0])
+        lib().oracle_rates(proc, C.byref(self.struct), chi.shape[0], _ptr(chi), _ptr(energy), _ptr(out))
+        return out
+
+    def qs_table_cdf(self, chi, xi):
+        """r that the QS table lookup maps to xi (forward map of the sampling)."""
+        return lib().oracle_qs_table_cdf(C.byref(self.struct), chi, xi)
+
+    def bw_table_cdf(self, chig, xi):
+        """r in [0, 1/2] that the BW table lookup maps to xi in [0, 1/2]."""
+        return lib().oracle_bw_table_cdf(C.byref(self.struct), chig, xi)
 
     def qs_sample_xi(self, chi, r):
         return lib().oracle_qs_sample_xi(C.byref(self.struct), chi, r)
@@ -477,7 +496,7 @@ def substep(t: OracleTables, species: dict, dt: float, seed: int, step: int,
         s = out[name]
         if new[name]:
             keys = list(s.keys())
-            add = {k: np.array([d[k] for d in new[name]], dtype=s[k].dtype) for k in keys}
+            add = {k: np.array([d.get(k, 0) for d in new[name]], dtype=s[k].dtype) for k in keys}
             s = {k: np.concatenate([s[k], add[k]]) for k in keys}
         result[name] = s
     result["fire"] = fire

@@ -356,3 +356,51 @@ void oracle_init_tau(int64_t n, const uint64_t *id, uint64_t seed, int64_t step,
 {
     for (int64_t i = 0; i < n; ++i) tau[i] = oracle_tau_draw(seed, id[i], step, PURPOSE_TAU_INIT);
 }
+
+/* rate lookups for n given (chi, energy) pairs: QS energy = gamma, BW energy = |p| */
+void oracle_rates(int proc, const oracle_tables *t, int64_t n, const double *chi, const double *energy,
+                  double *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = proc == 0 ? oracle_qs_rate(t, chi[i], energy[i]) : oracle_bw_rate(t, chi[i], energy[i]);
+}
+
+/* Forward maps of the table sampling: the r that the inverse-CDF lookup of
+ * §3.2 / §3.1 maps to xi (the interpolated row evaluated at xi on the same
+ * piecewise log-log (QS) or linear (BW) interpolant).  Used to measure the
+ * backward error of a sampled xi. */
+double oracle_qs_table_cdf(const oracle_tables *t, double chi, double xi)
+{
+    int N = t->qs_n_chi, M = t->qs_n_xi;
+    double lmin = log(t->qs_chi_min), lmax = log(t->qs_chi_max);
+    double c = chi < t->qs_chi_min ? t->qs_chi_min : (chi > t->qs_chi_max ? t->qs_chi_max : chi);
+    double lc = log(c);
+    int n = find_interval(lmin, lmax, N, lc);
+    double l0 = grid_ln(lmin, lmax, N, n), l1 = grid_ln(lmin, lmax, N, n + 1);
+    const double *a = t->qs_lnP + (size_t)n * M, *b = a + M;
+    double lx_min = log(t->qs_xi_min), lx = log(xi);
+    int m = find_interval(lx_min, 0.0, M, lx);
+    double lx0 = grid_ln(lx_min, 0.0, M, m), lx1 = grid_ln(lx_min, 0.0, M, m + 1);
+    double lp0 = a[m] + (lc - l0) * (b[m] - a[m]) / (l1 - l0);
+    double lp1 = a[m + 1] + (lc - l0) * (b[m + 1] - a[m + 1]) / (l1 - l0);
+    return exp(lp0 + (lx - lx0) * (lp1 - lp0) / (lx1 - lx0));
+}
+
+/* BW: xi of the sampled lepton in [0, 1/2] -> r in [0, 1/2] */
+double oracle_bw_table_cdf(const oracle_tables *t, double chig, double xi)
+{
+    int N = t->bw_n_chi, M = t->bw_n_xi;
+    double lmin = log(t->bw_chi_min), lmax = log(t->bw_chi_max);
+    double c = chig < t->bw_chi_min ? t->bw_chi_min : (chig > t->bw_chi_max ? t->bw_chi_max : chig);
+    double lc = log(c);
+    int n = find_interval(lmin, lmax, N, lc);
+    double l0 = grid_ln(lmin, lmax, N, n), l1 = grid_ln(lmin, lmax, N, n + 1);
+    const double *a = t->bw_P + (size_t)n * M, *b = a + M;
+    int m = (int)floor(xi * 2.0 * (M - 1));
+    if (m < 0) m = 0;
+    if (m > M - 2) m = M - 2;
+    double x0 = 0.5 * m / (M - 1), x1 = 0.5 * (m + 1) / (M - 1);
+    double p0 = a[m] + (lc - l0) * (b[m] - a[m]) / (l1 - l0);
+    double p1 = a[m + 1] + (lc - l0) * (b[m + 1] - a[m + 1]) / (l1 - l0);
+    return p0 + (xi - x0) * (p1 - p0) / (x1 - x0);
+}

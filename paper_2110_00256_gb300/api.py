@@ -1,0 +1,251 @@
+"""Python binding of libqed with the names of the C ABI (include/qed.h).
+
+Argument marshalling only: device memory comes from torch tensors, streams from
+torch.cuda; every step of the substep runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (QED_F32, QED_F64, QED_PROC_BW, QED_PROC_QS, QED_STAT_COUNT, FireList, QedError,
+                   SubstepOpts, TableAxis, TableParams, check, lib)
+
+__all__ = [
+    "QED_F32", "QED_F64", "QED_PROC_QS", "QED_PROC_BW", "QedError", "table_params", "Tables",
+    "SpeciesBuffers", "FireBuffers", "Stats", "qed_tables_generate", "qed_tables_create",
+    "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
+    "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
+    "qed_version",
+]
+
+FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype(prec: int):
+    return torch.float32 if prec == QED_F32 else torch.float64
+
+
+def table_params(qs_chi_min=1e-3, qs_chi_max=1e3, qs_n_chi=256, qs_n_xi=256, qs_xi_min=1e-12,
+                 bw_chi_min=2e-2, bw_chi_max=1e3, bw_n_chi=256, bw_n_xi=256) -> TableParams:
+    """Table axes; defaults are the paper's benchmark tables (§4)."""
+    return TableParams(TableAxis(qs_chi_min, qs_chi_max, qs_n_chi, qs_n_xi, qs_xi_min),
+                       TableAxis(bw_chi_min, bw_chi_max, bw_n_chi, bw_n_xi, 0.0))
+
+
+class Tables:
+    """Owning wrapper of a qed_tables* handle."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().qed_tables_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def params(self) -> TableParams:
+        p = TableParams()
+        check(lib().qed_tables_get_params(self.handle, C.byref(p)))
+        return p
+
+
+def qed_version() -> str:
+    return lib().qed_version().decode()
+
+
+def qed_tables_generate(params: TableParams, stream=None) -> Tables:
+    out = C.c_void_p()
+    check(lib().qed_tables_generate(C.byref(params), C.byref(out), _stream(stream)))
+    return Tables(out.value)
+
+
+def qed_tables_create(params: TableParams, qs_lnG, qs_lnP, bw_lnT, bw_P, stream=None) -> Tables:
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (qs_lnG, qs_lnP, bw_lnT, bw_P)]
+    exp = [params.qs.n_chi, params.qs.n_chi * params.qs.n_xi, params.bw.n_chi, params.bw.n_chi * params.bw.n_xi]
+    for a, n in zip(arrs, exp):
+        if a.size != n:
+            raise ValueError(f"table array has {a.size} entries, expected {n}")
+    out = C.c_void_p()
+    check(lib().qed_tables_create(C.byref(params), *[a.ctypes.data_as(C.c_void_p) for a in arrs],
+                                  C.byref(out), _stream(stream)))
+    return Tables(out.value)
+
+
+def qed_tables_copy_to_host(t: Tables) -> dict:
+    p = t.params
+    out = dict(qs_lnG=np.zeros(p.qs.n_chi), qs_lnP=np.zeros((p.qs.n_chi, p.qs.n_xi)),
+               bw_lnT=np.zeros(p.bw.n_chi), bw_P=np.zeros((p.bw.n_chi, p.bw.n_xi)))
+    check(lib().qed_tables_copy_to_host(t.handle, *[out[k].ctypes.data_as(C.c_void_p)
+                                                    for k in ("qs_lnG", "qs_lnP", "bw_lnT", "bw_P")]))
+    return out
+
+
+def qed_tables_save(t: Tables, path: str):
+    check(lib().qed_tables_save(t.handle, str(path).encode()))
+
+
+def qed_tables_load(path: str, stream=None) -> Tables:
+    out = C.c_void_p()
+    check(lib().qed_tables_load(str(path).encode(), C.byref(out), _stream(stream)))
+    return Tables(out.value)
+
+
+# ---------------------------------------------------------------------------------------
+# particle buffers (caller-owned device memory)
+# ---------------------------------------------------------------------------------------
+@dataclass
+class SpeciesBuffers:
+    """Structure-of-arrays species on the GPU with a fixed capacity."""
+    capacity: int
+    prec: int = QED_F32
+    device: str = "cuda"
+    arrays: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        dt = _dtype(self.prec)
+        cap = max(int(self.capacity), 1)
+        for k in FIELDS + ("tau", "tau_c", "weight"):
+            self.arrays[k] = torch.zeros(cap, dtype=dt, device=self.device)
+        self.arrays["id"] = torch.zeros(cap, dtype=torch.int64, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    def __getitem__(self, k):
+        return self.arrays[k]
+
+    def set(self, data: dict, n: int | None = None):
+        """Copy host/device arrays into [0, n) and set the live count."""
+        n = int(n if n is not None else len(data["px"]))
+        if n > self.capacity:
+            raise ValueError("more particles than capacity")
+        for k, v in data.items():
+            if k == "count":
+                continue
+            t = torch.as_tensor(v)
+            if k == "id":
+                t = t.to(torch.int64) if t.dtype != torch.uint64 else t.view(torch.int64)
+                self.arrays["id"][:n].copy_(t[:n].to(self.device))
+            else:
+                self.arrays[k][:n].copy_(t[:n].to(device=self.device, dtype=self.arrays[k].dtype))
+        self.count.fill_(n)
+        return self
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+    def struct(self) -> _lib.Species:
+        a = self.arrays
+        return _lib.Species(*[a[k].data_ptr() for k in FIELDS + ("tau", "tau_c", "weight", "id")],
+                            int(self.capacity), self.count.data_ptr())
+
+    def to_host(self) -> dict:
+        n = self.n()
+        out = {k: v[:n].cpu().numpy() for k, v in self.arrays.items()}
+        out["id"] = out["id"].view(np.uint64)
+        return out
+
+
+@dataclass
+class FireBuffers:
+    capacity: int
+    device: str = "cuda"
+
+    def __post_init__(self):
+        cap = max(int(self.capacity), 1)
+        self.idx = torch.zeros(cap, dtype=torch.int64, device=self.device)
+        self.chi = torch.zeros(cap, dtype=torch.float64, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    def struct(self) -> FireList:
+        return FireList(self.idx.data_ptr(), self.chi.data_ptr(), self.count.data_ptr(), int(self.capacity))
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+
+class Stats:
+    """Device counters (QED_STAT_*)."""
+
+    NAMES = ("qs_events", "bw_events", "photons_kept", "photons_discarded", "pairs", "bw_no_pair",
+             "dropped_capacity", "nonfinite", "fire_overflow")
+
+    def __init__(self, device="cuda"):
+        self.t = torch.zeros(QED_STAT_COUNT, dtype=torch.int64, device=device)
+
+    def as_dict(self) -> dict:
+        return dict(zip(self.NAMES, self.t.cpu().tolist()))
+
+
+def _opts(photon_threshold=0.0, stats: Stats | None = None) -> SubstepOpts:
+    return SubstepOpts(float(photon_threshold), 0, None, stats.t.data_ptr() if stats is not None else None)
+
+
+def qed_init_optical_depth(sp: SpeciesBuffers, seed: int, step: int = 0, stream=None):
+    s = sp.struct()
+    check(lib().qed_init_optical_depth(C.byref(s), sp.prec, seed, step, _stream(stream)))
+
+
+def qed_evolve_optical_depth(t: Tables, proc: int, sp: SpeciesBuffers, dt: float, fire: FireBuffers,
+                             stats: Stats | None = None, stream=None):
+    s, f = sp.struct(), fire.struct()
+    check(lib().qed_evolve_optical_depth(t.handle, proc, C.byref(s), float(dt), sp.prec, C.byref(f),
+                                         stats.t.data_ptr() if stats is not None else None,
+                                         _stream(stream)))
+
+
+def qed_generate_photons(t: Tables, leptons: SpeciesBuffers, photons: SpeciesBuffers, fire: FireBuffers,
+                         seed: int, step: int, photon_threshold=0.0, stats: Stats | None = None, stream=None):
+    a, b, f, o = leptons.struct(), photons.struct(), fire.struct(), _opts(photon_threshold, stats)
+    check(lib().qed_generate_photons(t.handle, C.byref(a), C.byref(b), C.byref(f), seed, step, C.byref(o),
+                                     leptons.prec, _stream(stream)))
+
+
+def qed_generate_pairs(t: Tables, photons: SpeciesBuffers, electrons: SpeciesBuffers,
+                       positrons: SpeciesBuffers, fire: FireBuffers, seed: int, step: int,
+                       stats: Stats | None = None, stream=None):
+    a, b, c, f, o = photons.struct(), electrons.struct(), positrons.struct(), fire.struct(), _opts(0.0, stats)
+    check(lib().qed_generate_pairs(t.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(f), seed, step,
+                                   C.byref(o), photons.prec, _stream(stream)))
+
+
+class SubstepCall:
+    """Pre-marshalled arguments of qed_substep, so that repeated calls (a timed
+    loop, a graph capture) pay no Python-side struct building."""
+
+    def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
+                 photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
+                 stats: Stats | None = None):
+        self.t = t
+        self.keep = (electrons, positrons, photons, fire, stats)
+        self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
+        self.fire = (FireList * 3)(*[f.struct() for f in fire])
+        self.opts = _opts(photon_threshold, stats)
+        self.dt = float(dt)
+        self.seed = int(seed)
+        self.prec = electrons.prec
+        self.fn = lib().qed_substep
+
+    def __call__(self, step: int, stream=None):
+        check(self.fn(self.t.handle, C.byref(self.e), C.byref(self.p), C.byref(self.g), self.dt, self.seed,
+                      int(step), C.byref(self.opts), self.prec, self.fire, _stream(stream)))
+
+
+def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
+                dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
+                stream=None):
+    SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats)(step, stream)

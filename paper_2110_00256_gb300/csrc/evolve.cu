@@ -1,0 +1,390 @@
+// evolve.cu -- optical-depth evolution (§3, Fig. scheme) as one batched,
+// persistent launch over many particle segments (species or patches), with
+// warp-ballot compaction of the firing particles, plus the optical-depth
+// initialisation.
+//
+// Layout: every segment is a structure of arrays in HBM.  A CTA walks tiles of
+// (256 threads x VEC) consecutive particles of one segment; each thread loads
+// VEC particles with one 16-byte load per component (float4 / double2), keeps
+// the 1-D rate tables of both processes in shared memory, and writes back only
+// the optical depth (and its Kahan word in FP32).  Tiles of all segments form
+// one index space; CTAs stride over it, so uneven segment sizes share the grid.
+#include <algorithm>
+
+#include "evolve.cuh"
+#include "physics.cuh"
+
+namespace qed {
+
+template <typename T, int VEC>
+struct Vec;
+template <>
+struct Vec<float, 4> {
+    using type = float4;
+};
+template <>
+struct Vec<double, 2> {
+    using type = double2;
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T *p, int64_t i, T (&out)[VEC])
+{
+    if constexpr (VEC == 1) {
+        out[0] = __ldcs(p + i);
+    } else {
+        using V = typename Vec<T, VEC>::type;
+        const V v = __ldcs(reinterpret_cast<const V *>(p + i));
+        if constexpr (VEC == 4) {
+            out[0] = v.x, out[1] = v.y, out[2] = v.z, out[3] = v.w;
+        } else {
+            out[0] = v.x, out[1] = v.y;
+        }
+    }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T *p, int64_t i, const T (&in)[VEC])
+{
+    if constexpr (VEC == 1) {
+        __stcs(p + i, in[0]);
+    } else {
+        using V = typename Vec<T, VEC>::type;
+        V v;
+        if constexpr (VEC == 4) {
+            v.x = in[0], v.y = in[1], v.z = in[2], v.w = in[3];
+        } else {
+            v.x = in[0], v.y = in[1];
+        }
+        __stcs(reinterpret_cast<V *>(p + i), v);
+    }
+}
+
+// one particle: chi, rate, optical-depth decrement; returns fire
+template <typename T>
+__device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_bw, const TablesView<T> &tv,
+                                           T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T dt,
+                                           T &tau, T &tc, T &chi_out, int &bad)
+{
+    T chi, rate;
+    if (proc == QED_PROC_QS) {
+        T gamma;
+        chi = chi_lepton(px, py, pz, ex, ey, ez, bx, by, bz, gamma);
+        rate = qs_rate(s_qs, tv.qs_G, chi, gamma);
+    } else {
+        T pm;
+        chi = chi_photon(px, py, pz, ex, ey, ez, bx, by, bz, pm);
+        rate = bw_rate(s_bw, tv.bw_T, chi, pm);
+    }
+    const bool ok = isfinite(chi) && !isnan(tau) && isfinite(rate);
+    bad += ok ? 0 : 1;
+    if (!ok) rate = T(0);
+    chi_out = chi;
+    if constexpr (sizeof(T) == 4) {
+        // Kahan-compensated decrement; tau - tc is the optical depth
+        if (!isfinite(tau)) return false;  // removed particle (tau = +inf)
+        const T y = d_fma(-rate, dt, -tc);
+        const T t = tau + y;
+        tc = (t - tau) - y;
+        tau = t;
+        return ok && (t < T(0) || (t == T(0) && tc > T(0)));
+    } else {
+        tau = tau - rate * dt;
+        return ok && tau < T(0);
+    }
+}
+
+template <typename T, int VEC, int MAXSEG>
+__global__ void __launch_bounds__(kEvolveThreads, 3)
+    evolve_kernel(const __grid_constant__ EvolveArgs<T, MAXSEG> a)
+{
+    __shared__ T s_qs[QED_MAX_TABLE_N];
+    __shared__ T s_bw[QED_MAX_TABLE_N];
+    __shared__ long long s_end[MAXSEG];  // inclusive prefix of tile counts
+    __shared__ long long s_n[MAXSEG];
+
+    for (int i = threadIdx.x; i < a.tab.qs_G.n; i += blockDim.x) s_qs[i] = a.tab.qs_G.ln_f[i];
+    for (int i = threadIdx.x; i < a.tab.bw_T.n; i += blockDim.x) s_bw[i] = a.tab.bw_T.ln_f[i];
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int s = 0; s < a.n_seg; ++s) {
+            long long n = *a.seg[s].count;
+            n = n < 0 ? 0 : (n > a.seg[s].capacity ? a.seg[s].capacity : n);
+            s_n[s] = n;
+            acc += (n + kEvolveTile<T, VEC> - 1) / kEvolveTile<T, VEC>;
+            s_end[s] = acc;
+        }
+    }
+    __syncthreads();
+    const long long total = a.n_seg ? s_end[a.n_seg - 1] : 0;
+    const unsigned lane = threadIdx.x & 31u;
+    int bad = 0;
+
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        int s = 0;
+        while (t >= s_end[s]) ++s;
+        const EvolveSeg<T> &sg = a.seg[s];
+        const long long first = t - (s ? s_end[s - 1] : 0);
+        const int64_t n = s_n[s];
+        const int64_t i0 = first * kEvolveTile<T, VEC> + (int64_t)threadIdx.x * VEC;
+
+        T px[VEC], py[VEC], pz[VEC], ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC], tau[VEC], tc[VEC];
+        const bool full = i0 + VEC <= n;
+        if (full) {
+            load_vec<T, VEC>(sg.px, i0, px);
+            load_vec<T, VEC>(sg.py, i0, py);
+            load_vec<T, VEC>(sg.pz, i0, pz);
+            load_vec<T, VEC>(sg.ex, i0, ex);
+            load_vec<T, VEC>(sg.ey, i0, ey);
+            load_vec<T, VEC>(sg.ez, i0, ez);
+            load_vec<T, VEC>(sg.bx, i0, bx);
+            load_vec<T, VEC>(sg.by, i0, by);
+            load_vec<T, VEC>(sg.bz, i0, bz);
+            load_vec<T, VEC>(sg.tau, i0, tau);
+            if constexpr (sizeof(T) == 4) load_vec<T, VEC>(sg.tau_c, i0, tc);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                const int64_t i = i0 + j;
+                const bool v = i < n;
+                px[j] = v ? sg.px[i] : T(0);
+                py[j] = v ? sg.py[i] : T(0);
+                pz[j] = v ? sg.pz[i] : T(0);
+                ex[j] = v ? sg.ex[i] : T(0);
+                ey[j] = v ? sg.ey[i] : T(0);
+                ez[j] = v ? sg.ez[i] : T(0);
+                bx[j] = v ? sg.bx[i] : T(0);
+                by[j] = v ? sg.by[i] : T(0);
+                bz[j] = v ? sg.bz[i] : T(0);
+                tau[j] = v ? sg.tau[i] : T(1);
+                if constexpr (sizeof(T) == 4) tc[j] = v ? sg.tau_c[i] : T(0);
+            }
+        }
+
+        bool fire[VEC];
+        T chi[VEC];
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            T c = sizeof(T) == 4 ? tc[j] : T(0);
+            fire[j] = evolve_one<T>(sg.proc, s_qs, s_bw, a.tab, px[j], py[j], pz[j], ex[j], ey[j], ez[j], bx[j],
+                                    by[j], bz[j], a.dt, tau[j], c, chi[j], bad);
+            tc[j] = c;
+            fire[j] = fire[j] && (i0 + j < n);
+            cnt += fire[j] ? 1 : 0;
+        }
+
+        if (full) {
+            store_vec<T, VEC>(sg.tau, i0, tau);
+            if constexpr (sizeof(T) == 4) store_vec<T, VEC>(sg.tau_c, i0, tc);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                if (i0 + j < n) {
+                    sg.tau[i0 + j] = tau[j];
+                    if constexpr (sizeof(T) == 4) sg.tau_c[i0 + j] = tc[j];
+                }
+            }
+        }
+
+        // warp-ballot compaction of the firing particles: one atomic per warp
+        if (__ballot_sync(0xffffffffu, cnt > 0)) {
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(sg.fire_count, (unsigned long long)wtot);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            long long pos = (long long)base + incl - cnt;
+            int over = 0;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                if (fire[j]) {
+                    if (pos < sg.fire_cap) {
+                        sg.fire_idx[pos] = i0 + j;
+                        sg.fire_chi[pos] = (double)chi[j];
+                    } else {
+                        ++over;
+                    }
+                    ++pos;
+                }
+            }
+            if (a.stats) warp_count(a.stats + QED_STAT_FIRE_OVERFLOW, over);
+        }
+    }
+    if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
+}
+
+// clamp the firing counters to their capacity once the evolution is done
+__global__ void clamp_fire_counts(unsigned long long *c0, int64_t cap0, unsigned long long *c1, int64_t cap1,
+                                  unsigned long long *c2, int64_t cap2)
+{
+    if (threadIdx.x == 0) {
+        if (c0 && *c0 > (unsigned long long)cap0) *c0 = cap0;
+        if (c1 && *c1 > (unsigned long long)cap1) *c1 = cap1;
+        if (c2 && *c2 > (unsigned long long)cap2) *c2 = cap2;
+    }
+}
+
+static int g_sm_count = 0;
+
+int sm_count()
+{
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+template <typename T, int VEC, int MAXSEG>
+static int evolve_grid(int64_t total_particles)
+{
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, evolve_kernel<T, VEC, MAXSEG>, kEvolveThreads, 0);
+        if (blocks_per_sm <= 0) blocks_per_sm = 1;
+    }
+    const int64_t tiles = (total_particles + kEvolveTile<T, VEC> - 1) / kEvolveTile<T, VEC>;
+    int64_t g = (int64_t)sm_count() * blocks_per_sm;
+    if (tiles < g) g = tiles < 1 ? 1 : tiles;
+    return (int)g;
+}
+
+template <typename T, int MAXSEG>
+qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t capacity_sum, int grid_override,
+                         cudaStream_t st)
+{
+    // the grid is sized from the capacities (counts live on the device); idle
+    // CTAs exit after reading the counts
+    if (vec_ok) {
+        constexpr int V = sizeof(T) == 4 ? 4 : 2;
+        const int g = grid_override > 0 ? grid_override : evolve_grid<T, V, MAXSEG>(capacity_sum);
+        evolve_kernel<T, V, MAXSEG><<<g, kEvolveThreads, 0, st>>>(a);
+    } else {
+        const int g = grid_override > 0 ? grid_override : evolve_grid<T, 1, MAXSEG>(capacity_sum);
+        evolve_kernel<T, 1, MAXSEG><<<g, kEvolveThreads, 0, st>>>(a);
+    }
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+template qed_status launch_evolve<float, 4>(const EvolveArgs<float, 4> &, bool, int64_t, int, cudaStream_t);
+template qed_status launch_evolve<double, 4>(const EvolveArgs<double, 4> &, bool, int64_t, int, cudaStream_t);
+template qed_status launch_evolve<float, kMaxSegments>(const EvolveArgs<float, kMaxSegments> &, bool, int64_t, int,
+                                                       cudaStream_t);
+template qed_status launch_evolve<double, kMaxSegments>(const EvolveArgs<double, kMaxSegments> &, bool, int64_t, int,
+                                                        cudaStream_t);
+
+static bool al16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+bool fill_seg(EvolveSeg<T> &g, const qed_species *sp, int proc, const qed_fire_list *fire)
+{
+    g.px = (const T *)sp->px, g.py = (const T *)sp->py, g.pz = (const T *)sp->pz;
+    g.ex = (const T *)sp->ex, g.ey = (const T *)sp->ey, g.ez = (const T *)sp->ez;
+    g.bx = (const T *)sp->bx, g.by = (const T *)sp->by, g.bz = (const T *)sp->bz;
+    g.tau = (T *)sp->tau;
+    g.tau_c = (T *)sp->tau_c;
+    g.count = sp->d_count;
+    g.capacity = sp->capacity;
+    g.fire_idx = fire->idx;
+    g.fire_chi = fire->chi;
+    g.fire_count = (unsigned long long *)fire->d_count;
+    g.fire_cap = fire->capacity;
+    g.proc = proc;
+    const void *ps[] = {sp->px, sp->py, sp->pz, sp->ex, sp->ey, sp->ez, sp->bx, sp->by, sp->bz, sp->tau};
+    bool ok = true;
+    for (const void *p : ps) ok = ok && al16(p);
+    if (sizeof(T) == 4) ok = ok && al16(sp->tau_c);
+    return ok;
+}
+
+template bool fill_seg<float>(EvolveSeg<float> &, const qed_species *, int, const qed_fire_list *);
+template bool fill_seg<double>(EvolveSeg<double> &, const qed_species *, int, const qed_fire_list *);
+
+qed_status check_fire(const qed_fire_list *f, const char *name)
+{
+    if (!f) QED_FAIL(QED_ERR_INVALID_ARG, "%s: fire list is NULL", name);
+    if (!f->idx || !f->chi || !f->d_count) QED_FAIL(QED_ERR_INVALID_ARG, "%s: fire list array is NULL", name);
+    if (f->capacity < 0) QED_FAIL(QED_ERR_INVALID_ARG, "%s: negative fire-list capacity", name);
+    return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// optical-depth initialisation: tau = -ln U(seed, (id, step, 2))
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void init_tau_kernel(T *tau, T *tau_c, const uint64_t *id, const int64_t *count, int64_t capacity,
+                                uint64_t seed, int64_t step)
+{
+    int64_t n = *count;
+    n = n < 0 ? 0 : (n > capacity ? capacity : n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        store_tau<T>(tau, tau_c, i, tau_draw(seed, id[i], step, kTauInit));
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" qed_status qed_init_optical_depth(const qed_species *sp, qed_precision prec, uint64_t seed, int64_t step,
+                                             void *stream)
+{
+    clear_error();
+    qed_status s = check_species(sp, "species", prec);
+    if (s) return s;
+    cudaStream_t st = as_stream(stream);
+    int64_t g = (sp->capacity + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    g = g < 1 ? 1 : (g > cap ? cap : g);
+    if (prec == QED_F32)
+        init_tau_kernel<float><<<(int)g, 256, 0, st>>>((float *)sp->tau, (float *)sp->tau_c, sp->id, sp->d_count,
+                                                       sp->capacity, seed, step);
+    else
+        init_tau_kernel<double><<<(int)g, 256, 0, st>>>((double *)sp->tau, nullptr, sp->id, sp->d_count,
+                                                        sp->capacity, seed, step);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+template <typename T>
+static qed_status evolve_one_species(const qed_tables *t, qed_process proc, const qed_species *sp, double dt,
+                                     const qed_fire_list *fire, int64_t *d_stats, cudaStream_t st)
+{
+    EvolveArgs<T, 4> a;
+    memset(&a, 0, sizeof(a));
+    a.n_seg = 1;
+    a.dt = (T)dt;
+    a.tab = make_view<T>(t);
+    a.stats = (long long *)d_stats;
+    const bool vec = fill_seg<T>(a.seg[0], sp, (int)proc, fire);
+    QED_CUDA_TRY(cudaMemsetAsync(fire->d_count, 0, sizeof(int64_t), st));
+    qed_status s = launch_evolve<T, 4>(a, vec, sp->capacity, 0, st);
+    if (s) return s;
+    clamp_fire_counts<<<1, 32, 0, st>>>((unsigned long long *)fire->d_count, fire->capacity, nullptr, 0, nullptr, 0);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+extern "C" qed_status qed_evolve_optical_depth(const qed_tables *t, qed_process proc, const qed_species *sp,
+                                               double dt, qed_precision prec, const qed_fire_list *fire,
+                                               int64_t *d_stats, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_tables(t))) return s;
+    if ((s = check_species(sp, "species", prec))) return s;
+    if ((s = check_fire(fire, "fire"))) return s;
+    if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", (int)proc);
+    if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    cudaStream_t st = as_stream(stream);
+    return prec == QED_F32 ? evolve_one_species<float>(t, proc, sp, dt, fire, d_stats, st)
+                           : evolve_one_species<double>(t, proc, sp, dt, fire, d_stats, st);
+}

@@ -1,0 +1,55 @@
+// evolve.cuh -- launch descriptors of the batched optical-depth evolution.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace qed {
+
+constexpr int kEvolveThreads = 256;
+template <typename T, int VEC>
+constexpr int64_t kEvolveTile = (int64_t)kEvolveThreads * VEC;
+
+// segments per launch of the batched (patch) evolution; the descriptors travel
+// as kernel parameters (__grid_constant__), so no device memory is involved
+constexpr int kMaxSegments = 64;
+
+template <typename T>
+struct EvolveSeg {
+    const T *px, *py, *pz, *ex, *ey, *ez, *bx, *by, *bz;
+    T *tau, *tau_c;
+    const int64_t *count;
+    int64_t capacity;
+    int64_t *fire_idx;
+    double *fire_chi;
+    unsigned long long *fire_count;
+    int64_t fire_cap;
+    int proc;
+};
+
+template <typename T, int MAXSEG>
+struct EvolveArgs {
+    EvolveSeg<T> seg[MAXSEG];
+    TablesView<T> tab;
+    long long *stats;
+    T dt;
+    int n_seg;
+};
+
+int sm_count();
+
+template <typename T, int MAXSEG>
+qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t capacity_sum, int grid_override,
+                         cudaStream_t st);
+
+template <typename T>
+bool fill_seg(EvolveSeg<T> &g, const qed_species *sp, int proc, const qed_fire_list *fire);
+
+qed_status check_fire(const qed_fire_list *f, const char *name);
+
+__global__ void clamp_fire_counts(unsigned long long *c0, int64_t cap0, unsigned long long *c1, int64_t cap1,
+                                  unsigned long long *c2, int64_t cap2);
+
+}  // namespace qed

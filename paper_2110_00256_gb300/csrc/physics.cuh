@@ -1,0 +1,224 @@
+// physics.cuh -- per-particle device functions of the QED substep (templated on
+// float / double): quantum parameters (§2), 1-D rate lookups (§3.1, §3.2),
+// 2-D inverse-CDF sampling (§3.1, §3.2) and the optical-depth reset.
+#pragma once
+
+#include "common.cuh"
+
+namespace qed {
+
+__device__ __forceinline__ float d_log(float x) { return logf(x); }
+__device__ __forceinline__ double d_log(double x) { return log(x); }
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_cbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double d_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float d_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double d_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// leading asymptotes of T outside the table (Eq. (t_func), read in the paper's
+// chi_gamma convention): T ~ 3 sqrt(3) / (16 sqrt(2)) exp(-8 / (3 chi)) for
+// small chi, T ~ C chi^{-1/3} with C = 15 3^{2/3} Gamma(2/3)^3 / (14 pi sqrt(3)
+// Gamma(1/3)) for large chi.
+constexpr double kTSmall = 0.22963966338592293;
+constexpr double kTLarge = 0.37961230854357125;
+
+// chi of a lepton, §2: chi^2 = (gamma E + p x B)^2 - (p.E)^2 in these units.
+// With n = p/|p| and E_perp = E - (n.E) n the same quantity is the sum of
+// squares |gamma E_perp + p x B|^2 + (n.E)^2 (expand gamma^2 = 1 + p^2 and use
+// p x B perpendicular to n), which avoids the cancellation of the difference
+// form when chi is small against gamma |E| + |p| |B|.  A particle at rest has
+// chi = |E|.  Returns chi and gamma; NaN inputs give NaN.
+template <typename T>
+__device__ __forceinline__ T chi_lepton(T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T &gamma)
+{
+    const T p2 = px * px + py * py + pz * pz;
+    gamma = d_sqrt(T(1) + p2);
+    const T pm = d_sqrt(p2);
+    const T inv = pm > T(0) ? T(1) / pm : T(0);
+    const T nx = px * inv, ny = py * inv, nz = pz * inv;
+    const T ne = nx * ex + ny * ey + nz * ez;
+    const T fx = gamma * (ex - ne * nx) + (py * bz - pz * by);
+    const T fy = gamma * (ey - ne * ny) + (pz * bx - px * bz);
+    const T fz = gamma * (ez - ne * nz) + (px * by - py * bx);
+    const T s = fx * fx + fy * fy + fz * fz + (pm > T(0) ? ne * ne : ex * ex + ey * ey + ez * ez);
+    return d_sqrt(s);
+}
+
+// chi_gamma of a photon, §2 (gamma -> |p|, v -> c n): chi_gamma = | |p| E_perp +
+// p x B |, the perpendicular part of |p| E + p x B.  Returns chi and |p|.
+template <typename T>
+__device__ __forceinline__ T chi_photon(T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T &pm)
+{
+    pm = d_sqrt(px * px + py * py + pz * pz);
+    const T inv = pm > T(0) ? T(1) / pm : T(0);
+    const T nx = px * inv, ny = py * inv, nz = pz * inv;
+    const T ne = nx * ex + ny * ey + nz * ez;
+    const T fx = pm * (ex - ne * nx) + (py * bz - pz * by);
+    const T fy = pm * (ey - ne * ny) + (pz * bx - px * bz);
+    const T fz = pm * (ez - ne * nz) + (px * by - py * bx);
+    return d_sqrt(fx * fx + fy * fy + fz * fz);
+}
+
+// log-log interpolation of a 1-D table held in `tab` (shared or global):
+// ln f(chi) = ln f_n + (ln chi - ln chi_n) (ln f_{n+1} - ln f_n) / (ln chi_{n+1} - ln chi_n),
+// n = clamp(floor((ln chi - ln chi_min) / d), 0, N - 2); chi clamped into the table.
+template <typename T>
+__device__ __forceinline__ T interp_ln(const T *tab, T lc, T ln_min, T inv_d, int n)
+{
+    T t = (lc - ln_min) * inv_d;
+    t = t < T(0) ? T(0) : (t > T(n - 1) ? T(n - 1) : t);
+    int i = (int)t;
+    i = i > n - 2 ? n - 2 : i;
+    const T f = t - T(i);
+    const T a = tab[i], b = tab[i + 1];
+    return d_fma(f, b - a, a);
+}
+
+// QS rate (Eq. (qs_total_cross)): (2/3) alpha G(chi) / gamma; G clamped to the
+// end values outside [chi_min, chi_max] (§3.2); chi == 0 gives 0.
+template <typename T>
+__device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T gamma)
+{
+    if (!(chi > T(0))) return T(0);
+    const T lnG = interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n);
+    return T(2.0 / 3.0 * kAlpha) * d_exp(lnG) / gamma;
+}
+
+// BW rate (Eq. (bw_cross_tot)): alpha chi T(chi) / gamma_g; the asymptotes of
+// Eq. (t_func) outside [chi_min, chi_max] (§3.1).
+template <typename T>
+__device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T pm)
+{
+    if (!(chi > T(0)) || !(pm > T(0))) return T(0);
+    T Tv;
+    if (chi < v.chi_min)
+        Tv = T(kTSmall) * d_exp(T(-8.0 / 3.0) / chi);
+    else if (chi > v.chi_max)
+        Tv = T(kTLarge) / d_cbrt(chi);
+    else
+        Tv = d_exp(interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n));
+    return T(kAlpha) * chi * Tv / pm;
+}
+
+// interpolated row value of a 2-D table at column m: v_n,m + w (v_{n+1},m - v_n,m)
+template <typename T>
+__device__ __forceinline__ T row_val(const T *r0, const T *r1, T w, int m)
+{
+    const T a = __ldg(r0 + m), b = __ldg(r1 + m);
+    return d_fma(w, b - a, a);
+}
+
+// locate the chi interval of a 2-D table (chi clamped into the table, §3.1/§3.2);
+// r0, r1 are the two rows, off their offset (for the difference table)
+template <typename T>
+__device__ __forceinline__ void locate_2d(const Table2D<T> &tb, T chi, const T *&r0, const T *&r1, T &w,
+                                          size_t &off)
+{
+    T c = chi < tb.chi_min ? tb.chi_min : (chi > tb.chi_max ? tb.chi_max : chi);
+    T t = (d_log(c) - tb.ln_min) * tb.inv_d;
+    t = t < T(0) ? T(0) : (t > T(tb.n_chi - 1) ? T(tb.n_chi - 1) : t);
+    int n = (int)t;
+    n = n > tb.n_chi - 2 ? tb.n_chi - 2 : n;
+    w = t - T(n);
+    off = (size_t)n * tb.n_xi;
+    r0 = tb.v + off;
+    r1 = r0 + tb.n_xi;
+}
+
+// largest m in [0, M-1] with P_m <= x on the interpolated row (binary search;
+// the row is non-decreasing), then clamped to [0, M-2]; m = 0 when x < P_0.
+template <typename T>
+__device__ __forceinline__ int search_row(const T *r0, const T *r1, T w, int M, T x)
+{
+    int lo = 0, hi = M;  // invariant: P_lo <= x (or lo == 0), P_hi > x (hi == M: sentinel)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (row_val(r0, r1, w, mid) <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo > M - 2 ? M - 2 : lo;
+}
+
+// QS inverse CDF (§3.2): ln P interpolated in ln chi, binary search on ln r, then
+// ln xi = ln xi_m + (ln r - ln P_m)(ln xi_{m+1} - ln xi_m)/(ln P_{m+1} - ln P_m).
+// The denominator is interpolated from the FP64-formed column differences, so
+// that it keeps its relative accuracy in the FP32 tables (where two neighbouring
+// entries share most of their digits); the same holds below xi_min, where the
+// first segment is extrapolated.
+template <typename T>
+__device__ __forceinline__ T qs_sample_xi(const Table2D<T> &tb, T chi, T r)
+{
+    const T *r0, *r1;
+    T w;
+    size_t off;
+    locate_2d(tb, chi, r0, r1, w, off);
+    const T lr = d_log(r);
+    const int m = search_row(r0, r1, w, tb.n_xi, lr);
+    const T p0 = row_val(r0, r1, w, m);
+    const T dp = row_val(tb.dv + off, tb.dv + off + tb.n_xi, w, m);  // P_{m+1} - P_m
+    const T x0 = tb.x0 + T(m) * tb.dx;
+    const T x1 = (m + 1 == tb.n_xi - 1) ? T(0) : tb.x0 + T(m + 1) * tb.dx;
+    if (!(dp > T(0))) return d_exp(x0);
+    T lx = x0 + (lr - p0) * (x1 - x0) / dp;
+    lx = lx > T(0) ? T(0) : lx;
+    return d_exp(lx);
+}
+
+// BW inverse CDF (§3.1): r <= 1/2 samples the electron, otherwise the positron
+// with r -> 1 - r; P interpolated in ln chi_g, binary search on r, linear in xi
+// (denominator from the column differences, as for QS).
+template <typename T>
+__device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, T r, bool &electron)
+{
+    electron = r <= T(0.5);
+    if (!electron) r = T(1) - r;
+    const T *r0, *r1;
+    T w;
+    size_t off;
+    locate_2d(tb, chi, r0, r1, w, off);
+    const int m = search_row(r0, r1, w, tb.n_xi, r);
+    const T p0 = row_val(r0, r1, w, m);
+    const T dp = row_val(tb.dv + off, tb.dv + off + tb.n_xi, w, m);
+    const T x0 = T(m) * tb.dx;
+    const T x1 = (m + 1 == tb.n_xi - 1) ? T(0.5) : T(m + 1) * tb.dx;
+    if (!(dp > T(0))) return x0;
+    T x = x0 + (r - p0) * (x1 - x0) / dp;
+    return x > T(0.5) ? T(0.5) : (x < T(0) ? T(0) : x);
+}
+
+// uniform for sampling in the working precision: FP64 as drawn; FP32 rounded
+// toward zero so that it stays in (0, 1)
+template <typename T>
+__device__ __forceinline__ T sample_uniform(double u);
+template <>
+__device__ __forceinline__ double sample_uniform<double>(double u) { return u; }
+template <>
+__device__ __forceinline__ float sample_uniform<float>(double u) { return __double2float_rz(u); }
+
+// store an FP64 optical depth: FP64 as is; FP32 as (tau, tau_c) with tau_c the
+// rounding residual (the optical depth is tau - tau_c)
+template <typename T>
+__device__ __forceinline__ void store_tau(T *tau, T *tau_c, int64_t i, double x);
+template <>
+__device__ __forceinline__ void store_tau<double>(double *tau, double *, int64_t i, double x) { tau[i] = x; }
+template <>
+__device__ __forceinline__ void store_tau<float>(float *tau, float *tau_c, int64_t i, double x)
+{
+    const float h = __double2float_rn(x);
+    tau[i] = h;
+    tau_c[i] = __double2float_rn((double)h - x);
+}
+
+// tau = -ln U, U the 53-bit uniform of (seed, (id, step, purpose)), in FP64 (§3)
+__device__ __forceinline__ double tau_draw(uint64_t seed, uint64_t id, int64_t step, uint32_t purpose)
+{
+    const U4 w = draw(seed, id, step, purpose);
+    return -log(uniform53(w.x, w.y));
+}
+
+}  // namespace qed

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI, no GPU needed: the library builds for sm_103a,
+loads, exports every entry point declared in include/*.h, and rejects bad
+arguments before touching the device.  Also checks the closed-form constants
+compiled into the kernels."""
+import ctypes as C
+import glob
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(qed_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_00256_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 14
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_declared_symbols():
+    from paper_2110_00256_gb300 import _lib
+    assert _declared() <= set(_lib.SIGNATURES)
+
+
+def test_version_and_error_message(lib):
+    assert b"sm_103a" in lib.qed_version()
+    assert lib.qed_last_error_message() is not None
+
+
+def test_argument_validation_without_gpu(lib):
+    from paper_2110_00256_gb300 import _lib
+    out = C.c_void_p()
+    # NULL params
+    assert lib.qed_tables_generate(None, C.byref(out), None) == 1
+    assert b"params" in lib.qed_last_error_message()
+    # bad axes
+    bad = _lib.TableParams(_lib.TableAxis(1.0, 0.5, 64, 64, 1e-12), _lib.TableAxis(0.02, 1e3, 64, 64, 0.0))
+    assert lib.qed_tables_generate(C.byref(bad), C.byref(out), None) == 1
+    too_big = _lib.TableParams(_lib.TableAxis(1e-3, 1e3, 4096, 64, 1e-12), _lib.TableAxis(0.02, 1e3, 64, 64, 0.0))
+    assert lib.qed_tables_generate(C.byref(too_big), C.byref(out), None) == 1
+    no_xi = _lib.TableParams(_lib.TableAxis(1e-3, 1e3, 64, 64, 0.0), _lib.TableAxis(0.02, 1e3, 64, 64, 0.0))
+    assert lib.qed_tables_generate(C.byref(no_xi), C.byref(out), None) == 1
+    # NULL handles / species
+    assert lib.qed_evolve_optical_depth(None, 0, None, 1.0, 0, None, None, None) == 1
+    assert lib.qed_substep(None, None, None, None, 1.0, 0, 0, None, 0, None, None) == 1
+    assert lib.qed_tables_load(b"/nonexistent/qed.tab", C.byref(out), None) == 6
+    assert lib.qed_tables_destroy(None) == 0
+
+
+def test_kernel_asymptote_constants_match_closed_forms():
+    src = open(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "physics.cuh")).read()
+    ts = float(re.search(r"kTSmall\s*=\s*([0-9.eE+-]+)", src).group(1))
+    tl = float(re.search(r"kTLarge\s*=\s*([0-9.eE+-]+)", src).group(1))
+    assert ts == pytest.approx(3 * math.sqrt(3) / (16 * math.sqrt(2)), rel=1e-15)
+    g23, g13 = math.gamma(2 / 3), math.gamma(1 / 3)
+    assert tl == pytest.approx(15 * 3 ** (2 / 3) * g23 ** 3 / (14 * math.pi * math.sqrt(3) * g13), rel=1e-15)
+    gen = open(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "tablegen.cu")).read()
+    c = float(re.search(r"\(([0-9.]+) /\* sqrt\(3\) / \(2 pi\) \*/\)", gen).group(1))
+    assert c == pytest.approx(math.sqrt(3) / (2 * math.pi), rel=1e-15)

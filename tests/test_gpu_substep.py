@@ -1,0 +1,233 @@
+"""GPU parity of the whole substep (evolution of electrons, positrons, photons;
+pair production; photon emission; appended secondaries) against the FP64
+oracle from identical seeded state, FP64 and FP32; capacity overflow; the
+photon keep-threshold; CUDA-graph capture; and the 10^8-particle FP32 workload
+checked on a sampled subset of particles."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import FIELDS, as_f64, check_substep_fp32, gpu_tables, sort_by_id, tau_bound, tau_eff
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SPECIES = ("electrons", "positrons", "photons")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2110_00256_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def tabs(api, oracle_tables_256):
+    return oracle_tables_256, gpu_tables(api, oracle_tables_256)
+
+
+def _inputs(n, seed, tau_scale=2e-4, n_pos=None):
+    from paper_2110_00256_gb300 import workloads
+    d = {"electrons": workloads.paper_benchmark(n, seed, 0),
+         "positrons": workloads.paper_benchmark(n if n_pos is None else n_pos, seed + 1, 10 ** 12),
+         "photons": workloads.paper_benchmark(n, seed + 2, 2 * 10 ** 12)}
+    for v in d.values():
+        v["tau"] *= tau_scale
+    return d
+
+
+def _run_gpu(api, t, host, prec, dt, seed, step, extra=3.0, threshold=0.0, caps=None):
+    bufs, fire = {}, []
+    for k in SPECIES:
+        n = len(host[k]["px"])
+        cap = caps[k] if caps else int(n * extra) + 64
+        b = api.SpeciesBuffers(cap, prec)
+        if n:
+            b.set(host[k])
+        bufs[k] = b
+        fire.append(api.FireBuffers(cap))
+    stats = api.Stats()
+    api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], dt, seed, step, fire,
+                    photon_threshold=threshold, stats=stats)
+    torch.cuda.synchronize()
+    return {k: bufs[k].to_host() for k in SPECIES}, stats.as_dict(), fire
+
+
+def _margin_ids(ot, host64, dt, tol, seed, step):
+    """ids of particles whose decision lies within the error bound, and their children."""
+    out = set()
+    for k, proc in (("electrons", 0), ("positrons", 0), ("photons", 1)):
+        tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt)
+        b = tau_bound(ot, proc, host64[k], chi, rate, dt, tol)
+        for pid in host64[k]["id"][np.abs(tn) <= b].tolist():
+            out.add(pid)
+            out |= set(oracle.child_ids(seed, pid, step))
+    return out
+
+
+def _compare(got, ref, prec_f32, tol, exclude=frozenset()):
+    worst = {}
+    for k in SPECIES:
+        g, r = sort_by_id(got[k]), sort_by_id({kk: ref[k][kk] for kk in got[k]})
+        if exclude:
+            keep_g = ~np.isin(g["id"], list(exclude))
+            keep_r = ~np.isin(r["id"], list(exclude))
+            g = {kk: v[keep_g] for kk, v in g.items()}
+            r = {kk: v[keep_r] for kk, v in r.items()}
+        assert np.array_equal(g["id"], r["id"]), f"{k}: id sets differ ({len(g['id'])} vs {len(r['id'])})"
+        gt = tau_eff(g, prec_f32)
+        fin = np.isfinite(r["tau"])
+        assert np.array_equal(np.isfinite(gt), fin), f"{k}: removed-particle mask"
+        pm = np.sqrt(r["px"] ** 2 + r["py"] ** 2 + r["pz"] ** 2)
+        e = 0.0
+        for c in ("px", "py", "pz"):
+            e = max(e, float(np.max(np.abs(g[c] - r[c]) / np.maximum(pm, 1e-300), initial=0)))
+        et = float(np.max(np.abs(gt[fin] - r["tau"][fin]) / np.maximum(np.abs(r["tau"][fin]), 1.0), initial=0))
+        for c in ("ex", "ey", "ez", "bx", "by", "bz", "weight"):
+            assert np.array_equal(g[c].astype(np.float64), r[c]), f"{k}: {c} copied exactly"
+        worst[k] = (e, et)
+        assert e <= tol, f"{k}: momentum rel err {e:.3e}"
+        assert et <= tol, f"{k}: tau err {et:.3e}"
+    return worst
+
+
+def test_substep_fp64_parity(api, tabs):
+    ot, t = tabs
+    host = _inputs(100_000, 11)
+    h64 = {k: as_f64(v, np.float64) for k, v in host.items()}
+    got, st, _ = _run_gpu(api, t, host, api.QED_F64, dt=10.0, seed=99, step=3)
+    ref = oracle.substep(ot, h64, dt=10.0, seed=99, step=3)
+    assert st["qs_events"] > 100 and st["pairs"] > 100
+    assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0
+    assert ref["n_new"]["photons"] == st["photons_kept"]
+    assert ref["n_new"]["electrons"] == st["pairs"]
+    excl = _margin_ids(ot, h64, 10.0, 1e-12, 99, 3)
+    assert len(excl) <= 9
+    _compare(got, ref, False, 1e-12, exclude=excl)
+
+
+def test_substep_fp32_parity(api, tabs):
+    ot, t = tabs
+    host = _inputs(50_000, 21)
+    h32 = {k: as_f64(v, np.float32) for k, v in host.items()}
+    got, st, fire = _run_gpu(api, t, host, api.QED_F32, dt=10.0, seed=7, step=1)
+    fl = {k: (f.idx[:f.n()].cpu().numpy(), f.chi[:f.n()].cpu().numpy()) for k, f in zip(SPECIES, fire)}
+    rep = check_substep_fp32(ot, h32, got, fl, 10.0, 7, 1)
+    assert rep["events"] > 200
+    assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0
+    print("fp32 substep:", rep)
+
+
+def test_energy_conservation_and_threshold(api, tabs):
+    ot, t = tabs
+    host = _inputs(50_000, 31)
+    got, st, _ = _run_gpu(api, t, host, api.QED_F64, dt=10.0, seed=3, step=0, threshold=0.0)
+
+    def energy(s):
+        e = 0.0
+        for k in ("electrons", "positrons"):
+            d = s[k]
+            e += np.sum(d["weight"] * np.sqrt(1 + d["px"] ** 2 + d["py"] ** 2 + d["pz"] ** 2))
+        d = s["photons"]
+        return e + np.sum(d["weight"] * np.sqrt(d["px"] ** 2 + d["py"] ** 2 + d["pz"] ** 2))
+
+    h64 = {k: as_f64(v, np.float64) for k, v in host.items()}
+    assert energy(got) == pytest.approx(energy(h64), rel=1e-12)
+    # with the keep-threshold (§5) photons below 2 m_e c^2 are discarded, leptons still recoil
+    got2, st2, _ = _run_gpu(api, t, host, api.QED_F64, dt=10.0, seed=3, step=0, threshold=2.0)
+    ref2 = oracle.substep(ot, h64, dt=10.0, seed=3, step=0, photon_threshold=2.0)
+    assert st2["photons_discarded"] > 0
+    assert st2["photons_kept"] + st2["photons_discarded"] == st2["qs_events"]
+    assert len(got2["photons"]["px"]) == len(ref2["photons"]["px"])
+
+
+def test_capacity_overflow_leaves_events_for_next_step(api, tabs):
+    ot, t = tabs
+    n = 20_000
+    host = _inputs(n, 41, tau_scale=1e-3)
+    caps = {"electrons": n + 5, "positrons": n + 5, "photons": n + 7}
+    got, st, _ = _run_gpu(api, t, host, api.QED_F64, dt=10.0, seed=5, step=0, caps=caps)
+    for k in SPECIES:
+        assert len(got[k]["px"]) <= caps[k]
+    assert st["dropped_capacity"] > 0
+    # every event either ran or left its parent untouched with tau < 0
+    h64 = {k: as_f64(v, np.float64) for k, v in host.items()}
+    ref = oracle.substep(ot, h64, dt=10.0, seed=5, step=0)
+    fired_e = ref["fire"]["electrons"].sum()
+    e = sort_by_id(got["electrons"])
+    e0 = e["id"] < n
+    still_neg = (e["tau"][e0] < 0).sum()
+    assert st["qs_events"] + st["dropped_capacity"] >= fired_e
+    assert still_neg > 0
+    # placeholders written into partially reserved slots are removed particles
+    for k in ("electrons", "positrons"):
+        d = got[k]
+        dead = d["id"] == np.uint64(0xFFFFFFFFFFFFFFFF)
+        assert np.all(d["weight"][dead] == 0) and np.all(np.isinf(d["tau"][dead]))
+
+
+def test_substep_graph_capture_matches_eager(api, tabs):
+    ot, t = tabs
+    host = _inputs(30_000, 51)
+    eager, _, _ = _run_gpu(api, t, host, api.QED_F32, dt=10.0, seed=8, step=4)
+    bufs, fire = {}, []
+    for k in SPECIES:
+        b = api.SpeciesBuffers(3 * 30_000 + 64, api.QED_F32).set(host[k])
+        bufs[k] = b
+        fire.append(api.FireBuffers(3 * 30_000 + 64))
+    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, 10.0, 8)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            call(4, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for k in SPECIES:
+        a, b = sort_by_id(eager[k]), sort_by_id(bufs[k].to_host())
+        assert np.array_equal(a["id"], b["id"])
+        for c in ("px", "py", "pz", "tau", "tau_c"):
+            assert np.array_equal(a[c], b[c]), (k, c)
+
+
+def test_full_size_fp32_workload_sampled(api, tabs):
+    """10^8 particles (5e7 electrons + 5e7 photons, the paper's §4 distribution),
+    one FP32 substep in the benchmark's launch configuration; 2e5 sampled
+    particles are recomputed by the oracle from their pre-step state."""
+    from paper_2110_00256_gb300 import workloads
+    ot, t = tabs
+    n = 50_000_000
+    dev = {"electrons": workloads.paper_benchmark_torch(n, 1, 0),
+           "photons": workloads.paper_benchmark_torch(n, 2, 2 * 10 ** 12)}
+    extra = 2_000_000
+    bufs = {}
+    for k, d in dev.items():
+        b = api.SpeciesBuffers(n + extra, api.QED_F32)
+        for c, v in d.items():
+            b.arrays[c][:n].copy_(v)
+        b.count.fill_(n)
+        bufs[k] = b
+    bufs["positrons"] = api.SpeciesBuffers(extra, api.QED_F32)
+    del dev
+    fire = [api.FireBuffers(bufs[k].capacity) for k in SPECIES]
+    idx = workloads.subsample_ids(n, 200_000, 5)
+    ti = torch.as_tensor(idx, device="cuda")
+    pre = {k: {c: bufs[k].arrays[c][ti].cpu().numpy() for c in FIELDS + ("tau", "tau_c", "weight", "id")}
+           for k in ("electrons", "photons")}
+    stats = api.Stats()
+    api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 77, 0, fire, stats=stats)
+    torch.cuda.synchronize()
+    st = stats.as_dict()
+    assert st["nonfinite"] == 0 and st["dropped_capacity"] == 0 and st["fire_overflow"] == 0
+    assert st["qs_events"] > 0 and st["pairs"] > 0
+    for k, proc in (("electrons", 0), ("photons", 1)):
+        p = {c: v.astype(np.float64) if c != "id" else v.view(np.uint64) for c, v in pre[k].items()}
+        tau_new, chi, rate, f = oracle.evolve(proc, ot, p, 10.0)
+        bound = tau_bound(ot, proc, p, chi, rate, 10.0, 1e-5)
+        post_tau = bufs[k].arrays["tau"][ti].cpu().double().numpy() - bufs[k].arrays["tau_c"][ti].cpu().double().numpy()
+        fl = fire[0 if k == "electrons" else 2]
+        gpu_fired = np.isin(idx, fl.idx[:fl.n()].cpu().numpy())
+        assert np.all(np.abs(tau_new[gpu_fired != f]) <= bound[gpu_fired != f])
+        quiet = ~f & ~gpu_fired
+        assert np.all(np.abs(post_tau[quiet] - tau_new[quiet]) <= bound[quiet]), k
+        assert f.sum() > 0
