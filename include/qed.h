@@ -212,6 +212,34 @@ qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        uint64_t seed, int64_t step, const qed_substep_opts *opts,
                        qed_precision prec, const qed_fire_list *fire, void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* the substep without caller-provided working memory                        */
+/* ------------------------------------------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: codes whose GPU memory is
+ * owned by their own pool allocator, callers that must not trigger the device
+ * synchronisation that cudaMalloc / cudaFree imply in the middle of a time step,
+ * and runtimes that forbid allocations after start-up.
+ *
+ * Same arguments and results as qed_substep, without `fire`: the three firing
+ * lists live in a fixed array compiled into libqed (QED_NOALLOC_MAX_PARTICLES
+ * entries of index + chi, about 16 MiB), which every GPU that loads the
+ * library holds until the process exits.  The three species' capacities
+ * together may not exceed QED_NOALLOC_MAX_PARTICLES (QED_ERR_INVALID_ARG
+ * otherwise).  No allocation happens in this call.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  All calls share the one array (the firing counts are zeroed on the
+ * stream at the start of each call, the lists keep the last call's contents):
+ * calls that may overlap on the GPU -- different streams, or different host
+ * threads -- race and must be serialised by the caller. */
+#define QED_NOALLOC_MAX_PARTICLES (1 << 20)
+qed_status qed_substep_noalloc(const qed_tables *t, const qed_species *electrons,
+                               const qed_species *positrons, const qed_species *photons, double dt,
+                               uint64_t seed, int64_t step, const qed_substep_opts *opts,
+                               qed_precision prec, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

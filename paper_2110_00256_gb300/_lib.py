@@ -79,7 +79,10 @@ SIGNATURES = {
                                 C.POINTER(FireList), _U64, _I64, C.POINTER(SubstepOpts), _S, _P]),
     "qed_substep": (_S, [_P, C.POINTER(Species), C.POINTER(Species), C.POINTER(Species), _D, _U64, _I64,
                          C.POINTER(SubstepOpts), _S, C.POINTER(FireList), _P]),
+    "qed_substep_noalloc": (_S, [_P, C.POINTER(Species), C.POINTER(Species), C.POINTER(Species), _D, _U64,
+                                 _I64, C.POINTER(SubstepOpts), _S, _P]),
 }
+QED_NOALLOC_MAX_PARTICLES = 1 << 20
 
 _lock = threading.Lock()
 _lib = None

@@ -20,7 +20,7 @@ __all__ = [
     "SpeciesBuffers", "FireBuffers", "Stats", "qed_tables_generate", "qed_tables_create",
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
-    "qed_version",
+    "qed_substep_noalloc", "qed_version",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -249,3 +249,15 @@ def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
                 stream=None):
     SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats)(step, stream)
+
+
+def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
+                        photons: SpeciesBuffers, dt: float, seed: int, step: int, photon_threshold=0.0,
+                        stats: Stats | None = None, stream=None):
+    """qed_substep without caller-provided firing lists, for callers that cannot
+    allocate device memory: the lists live in a fixed array inside libqed, so the
+    three capacities together are limited to QED_NOALLOC_MAX_PARTICLES and calls
+    that overlap on the GPU race (see include/qed.h)."""
+    e, p, g, o = electrons.struct(), positrons.struct(), photons.struct(), _opts(photon_threshold, stats)
+    check(lib().qed_substep_noalloc(t.handle, C.byref(e), C.byref(p), C.byref(g), float(dt), int(seed),
+                                    int(step), C.byref(o), electrons.prec, _stream(stream)))
