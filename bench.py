@@ -68,9 +68,20 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_record(kernel_src: str):
+KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "physics.cuh", "common.cuh")
+
+
+def kernel_hash() -> str:
+    """Hash of the sources the evolution kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record():
     """DRAM bytes per particle of the evolution kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the kernel's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "evolve_kernel_fp32_traffic.txt")
     try:
         rec = {}
@@ -78,8 +89,7 @@ def traffic_record(kernel_src: str):
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
-        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") != h:
+        if rec.get("kernel_sources_sha256_16") != kernel_hash():
             return None
         return float(rec["dram_bytes_per_particle"])
     except Exception:
@@ -316,7 +326,7 @@ def gpu_main(args):
     ev_mean = sum(ev) / len(ev)
     hbm, which = peaks()
     ach = BYTES_F32 * r["n_before"] / (ev_mean * 1e-3) / 1e9
-    traffic_bpp = traffic_record(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "evolve.cu"))
+    traffic_bpp = traffic_record()
     roofline = {"bound": "hbm", "kernel": "evolve_kernel<float,4>", "achieved": round(ach, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_kind": which,
                 "traffic": (traffic_bpp * r["n_before"]) if traffic_bpp else None,

@@ -160,9 +160,8 @@ __global__ void __launch_bounds__(256) bw_event_kernel(const __grid_constant__ E
         const uint64_t pid = valid ? P.id[i] : 0;
 
         const U4 w = draw(a.seed, pid, a.step, kSample);
-        const T r = sample_uniform<T>(uniform53(w.x, w.y));
         bool electron = true;
-        const T xs = valid ? bw_sample_xi<T>(a.tab, chi, r, electron) : T(0);
+        const T xs = valid ? bw_sample_xi<T>(a.tab, chi, uniform53(w.x, w.y), electron) : T(0);
         const T xm = electron ? xs : T(1) - xs;
         const T xp = electron ? T(1) - xs : xs;
 

@@ -103,6 +103,15 @@ __device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T
     return T(kAlpha) * chi * Tv / pm;
 }
 
+// uniform for sampling in the working precision: FP64 as drawn; FP32 rounded
+// toward zero so that it stays in (0, 1)
+template <typename T>
+__device__ __forceinline__ T sample_uniform(double u);
+template <>
+__device__ __forceinline__ double sample_uniform<double>(double u) { return u; }
+template <>
+__device__ __forceinline__ float sample_uniform<float>(double u) { return __double2float_rz(u); }
+
 // interpolated row value of a 2-D table at column m: v_n,m + w (v_{n+1},m - v_n,m)
 template <typename T>
 __device__ __forceinline__ T row_val(const T *r0, const T *r1, T w, int m)
@@ -173,10 +182,11 @@ __device__ __forceinline__ T qs_sample_xi(const Table2D<T> &tb, T chi, T r)
 // with r -> 1 - r; P interpolated in ln chi_g, binary search on r, linear in xi
 // (denominator from the column differences, as for QS).
 template <typename T>
-__device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, T r, bool &electron)
+__device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, double u, bool &electron)
 {
-    electron = r <= T(0.5);
-    if (!electron) r = T(1) - r;
+    // split on the FP64 draw, then round the folded value (keeps 1 - u accurate)
+    electron = u <= 0.5;
+    const T r = sample_uniform<T>(electron ? u : 1.0 - u);
     const T *r0, *r1;
     T w;
     size_t off;
@@ -191,14 +201,6 @@ __device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, T r, bool
     return x > T(0.5) ? T(0.5) : (x < T(0) ? T(0) : x);
 }
 
-// uniform for sampling in the working precision: FP64 as drawn; FP32 rounded
-// toward zero so that it stays in (0, 1)
-template <typename T>
-__device__ __forceinline__ T sample_uniform(double u);
-template <>
-__device__ __forceinline__ double sample_uniform<double>(double u) { return u; }
-template <>
-__device__ __forceinline__ float sample_uniform<float>(double u) { return __double2float_rz(u); }
 
 // store an FP64 optical depth: FP64 as is; FP32 as (tau, tau_c) with tau_c the
 // rounding residual (the optical depth is tau - tau_c)

@@ -204,7 +204,7 @@ def check_substep_fp32(ot, host, got, fire_lists, dt, seed, step, rtol_r=1e-5):
                 xs = (km if electron else kp) / (pm - 2.0)
                 rs = r if electron else 1.0 - r
                 rr = ot.bw_table_cdf(chi_gpu[int(j)], xs)
-                report["worst_r"] = max(report["worst_r"], abs(rr - rs) / max(rs, 1e-3))
-                assert abs(rr - rs) <= rtol_r * max(rs, 1e-3), (name, pid, rs, rr)
+                report["worst_r"] = max(report["worst_r"], abs(rr - rs) / rs)
+                assert abs(rr - rs) <= rtol_r * rs + 1e-12, (name, pid, rs, rr)
                 assert gw[j] == 0 and np.isinf(gt[j])
     return report
