@@ -82,6 +82,8 @@ typedef struct {
     uint64_t *id;
     int64_t capacity;
     int64_t *d_count;
+    void *x, *y, *z; /* optional positions (element type as px; NULL when not tracked):
+                        products inherit their parent's position */
 } qed_species;
 
 /* Device list of the particles whose optical depth went negative in the
@@ -110,12 +112,18 @@ enum {
 typedef struct {
     double photon_threshold; /* photons with gamma_g below this are not kept, the emitter
                                 still recoils (§5); 0 keeps every photon                     */
-    int32_t sampler;         /* 0: 2-D inverse-CDF tables; 1: MLP surrogate (qed_mlp)         */
-    const void *mlp;         /* qed_mlp* when sampler == 1                                    */
+    int32_t sampler;         /* 0: 2-D inverse-CDF tables; 1: learned sampler (qed_mlp)       */
+    const void *mlp;         /* the qed_mlp* when sampler == 1                                */
     int64_t *d_stats;        /* device int64[QED_STAT_COUNT], or NULL                         */
     void *evolve_begin;      /* optional cudaEvent_t recorded on the stream right before the
                                 evolution launch of qed_substep (timing); NULL: none          */
     void *evolve_end;        /* optional cudaEvent_t recorded right after that launch         */
+    int64_t *d_step;         /* optional device int64: if set, the step number (a Philox
+                                counter word) is read from it instead of the `step`
+                                argument; qed_substep and qed_substep_batched add one to it
+                                at the end, so that one captured graph replays many steps   */
+    int32_t evolve_threads;  /* evolution launch shape: threads per CTA (128, 256 or 512) and */
+    int32_t evolve_ctas_per_sm; /* CTAs per SM (1..8); 0 = the library's default / tuned   */
 } qed_substep_opts;
 
 /* ------------------------------------------------------------------------- */
@@ -211,6 +219,51 @@ qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        const qed_species *positrons, const qed_species *photons, double dt,
                        uint64_t seed, int64_t step, const qed_substep_opts *opts,
                        qed_precision prec, const qed_fire_list *fire, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* learned sampler (stands in for the 2-D tables of §3.1, §3.2)              */
+/* ------------------------------------------------------------------------- */
+/* Two small networks, one per process, each 2 -> 64 -> 64 -> 1 with the tanh
+ * form of GELU, bf16 weights and FP32 accumulation; the 64x64 layer runs on the
+ * tensor cores.  Input features: x1 = ln chi scaled to [-1, 1] over the
+ * tables' chi range (chi clamped into it), x2 = 2 U - 1 (QS) or 2 (2 min(U,
+ * 1 - U)) - 1 (BW).  Outputs: QS, y = ln xi - 3 ln U (xi = exp(min(y + 3 ln U,
+ * 0))); BW, y = the fraction of the lepton that U selects (U <= 1/2: the
+ * electron, as in §3.1), clamped to [0, 1/2].  Trained by the library's own
+ * forward/backward kernels with Adam on the mean squared error of y against
+ * (chi, U, xi) samples, xi typically from qed_table_sample on fine FP64 tables.
+ * qed_substep / qed_generate_* use it when opts->sampler == 1 and opts->mlp
+ * points to a qed_mlp.  Parameter vector: QED_MLP_PARAMS floats, W1[64][2],
+ * b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define QED_MLP_PARAMS 4417
+typedef struct qed_mlp qed_mlp; /* opaque, library-owned */
+
+/* Both networks, Glorot-uniform weights drawn from Philox(seed), zero biases;
+ * the input scaling takes the chi ranges of `t`.  Synchronises `stream`. */
+qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp **out, void *stream);
+qed_status qed_mlp_destroy(qed_mlp *m);
+/* FP32 master parameters of one network to / from host memory (set also
+ * refreshes the bf16 copy and clears the Adam moments; synchronous). */
+qed_status qed_mlp_get_params(const qed_mlp *m, qed_process proc, float *host_params);
+qed_status qed_mlp_set_params(qed_mlp *m, qed_process proc, const float *host_params, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error
+ * of a batch: device arrays chi[n], u[n], xi[n] (FP64; for BW xi is the
+ * electron's fraction chi_-/chi_g).  d_loss (device float, may be NULL)
+ * receives the batch loss before the step.  Calls on one network must not
+ * overlap. */
+qed_status qed_mlp_train_step(qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                              const double *d_xi, int64_t n, float lr, float *d_loss, void *stream);
+/* Gradient of the batch loss with respect to the parameter vector (device
+ * float[QED_MLP_PARAMS]), no update. */
+qed_status qed_mlp_gradients(qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                             const double *d_xi, int64_t n, float *d_grad, float *d_loss, void *stream);
+/* Batch inference: xi[i] for (chi[i], u[i]) (QS: chi_gamma/chi; BW: the
+ * electron's chi_-/chi_g), device FP64 arrays. */
+qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                          int64_t n, double *d_xi, void *stream);
+/* The same through the 2-D tables (§3.1, §3.2) in the given precision. */
+qed_status qed_table_sample(const qed_tables *t, qed_process proc, qed_precision prec, const double *d_chi,
+                            const double *d_u, int64_t n, double *d_xi, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* the substep without caller-provided working memory                        */

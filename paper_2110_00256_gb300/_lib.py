@@ -42,7 +42,8 @@ class TableParams(C.Structure):
 class Species(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz",
                                           "tau", "tau_c", "weight", "id")] + \
-               [("capacity", C.c_int64), ("d_count", C.c_void_p)]
+               [("capacity", C.c_int64), ("d_count", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("z", C.c_void_p)]
 
 
 class FireList(C.Structure):
@@ -52,7 +53,8 @@ class FireList(C.Structure):
 
 class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
-                ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p)]
+                ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
+                ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -81,7 +83,16 @@ SIGNATURES = {
                          C.POINTER(SubstepOpts), _S, C.POINTER(FireList), _P]),
     "qed_substep_noalloc": (_S, [_P, C.POINTER(Species), C.POINTER(Species), C.POINTER(Species), _D, _U64,
                                  _I64, C.POINTER(SubstepOpts), _S, _P]),
+    "qed_mlp_create": (_S, [_P, _U64, C.POINTER(_P), _P]),
+    "qed_mlp_destroy": (_S, [_P]),
+    "qed_mlp_get_params": (_S, [_P, _S, _P]),
+    "qed_mlp_set_params": (_S, [_P, _S, _P, _P]),
+    "qed_mlp_train_step": (_S, [_P, _S, _P, _P, _P, _I64, C.c_float, _P, _P]),
+    "qed_mlp_gradients": (_S, [_P, _S, _P, _P, _P, _I64, _P, _P, _P]),
+    "qed_mlp_sample": (_S, [_P, _S, _P, _P, _I64, _P, _P]),
+    "qed_table_sample": (_S, [_P, _S, _S, _P, _P, _I64, _P, _P]),
 }
+QED_MLP_PARAMS = 4417
 QED_NOALLOC_MAX_PARTICLES = 1 << 20
 
 _lock = threading.Lock()

@@ -20,7 +20,7 @@ __all__ = [
     "SpeciesBuffers", "FireBuffers", "Stats", "qed_tables_generate", "qed_tables_create",
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
-    "qed_substep_noalloc", "qed_version",
+    "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -115,12 +115,14 @@ class SpeciesBuffers:
     capacity: int
     prec: int = QED_F32
     device: str = "cuda"
+    positions: bool = False
     arrays: dict = field(default_factory=dict)
 
     def __post_init__(self):
         dt = _dtype(self.prec)
         cap = max(int(self.capacity), 1)
-        for k in FIELDS + ("tau", "tau_c", "weight"):
+        names = FIELDS + ("tau", "tau_c", "weight") + (("x", "y", "z") if self.positions else ())
+        for k in names:
             self.arrays[k] = torch.zeros(cap, dtype=dt, device=self.device)
         self.arrays["id"] = torch.zeros(cap, dtype=torch.int64, device=self.device)
         self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
@@ -150,8 +152,9 @@ class SpeciesBuffers:
 
     def struct(self) -> _lib.Species:
         a = self.arrays
+        pos = [a[k].data_ptr() for k in ("x", "y", "z")] if self.positions else [None, None, None]
         return _lib.Species(*[a[k].data_ptr() for k in FIELDS + ("tau", "tau_c", "weight", "id")],
-                            int(self.capacity), self.count.data_ptr())
+                            int(self.capacity), self.count.data_ptr(), *pos)
 
     def to_host(self) -> dict:
         n = self.n()
@@ -229,12 +232,15 @@ class SubstepCall:
 
     def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                  photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
-                 stats: Stats | None = None):
+                 stats: Stats | None = None, mlp: "Mlp | None" = None):
         self.t = t
-        self.keep = (electrons, positrons, photons, fire, stats)
+        self.keep = (electrons, positrons, photons, fire, stats, mlp)
         self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
         self.fire = (FireList * 3)(*[f.struct() for f in fire])
         self.opts = _opts(photon_threshold, stats)
+        if mlp is not None:
+            self.opts.sampler = 1
+            self.opts.mlp = mlp.handle.value
         self.dt = float(dt)
         self.seed = int(seed)
         self.prec = electrons.prec
@@ -247,8 +253,8 @@ class SubstepCall:
 
 def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
-                stream=None):
-    SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats)(step, stream)
+                stream=None, mlp: "Mlp | None" = None):
+    SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp)(step, stream)
 
 
 def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
@@ -261,3 +267,73 @@ def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: Species
     e, p, g, o = electrons.struct(), positrons.struct(), photons.struct(), _opts(photon_threshold, stats)
     check(lib().qed_substep_noalloc(t.handle, C.byref(e), C.byref(p), C.byref(g), float(dt), int(seed),
                                     int(step), C.byref(o), electrons.prec, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------
+# learned sampler
+# ---------------------------------------------------------------------------------------
+class Mlp:
+    """Owning wrapper of a qed_mlp* (the two networks, QS and BW)."""
+
+    NPARAM = _lib.QED_MLP_PARAMS
+
+    def __init__(self, tables: Tables, seed: int = 0, stream=None):
+        out = C.c_void_p()
+        check(lib().qed_mlp_create(tables.handle, int(seed), C.byref(out), _stream(stream)))
+        self.handle = out
+        self.tables = tables
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().qed_mlp_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def get_params(self, proc: int) -> np.ndarray:
+        out = np.zeros(self.NPARAM, dtype=np.float32)
+        check(lib().qed_mlp_get_params(self.handle, proc, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, proc: int, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.NPARAM
+        check(lib().qed_mlp_set_params(self.handle, proc, p.ctypes.data_as(C.c_void_p), _stream(stream)))
+
+    def train_step(self, proc: int, chi: torch.Tensor, u: torch.Tensor, xi: torch.Tensor, lr: float,
+                   loss: torch.Tensor | None = None, stream=None):
+        check(lib().qed_mlp_train_step(self.handle, proc, chi.data_ptr(), u.data_ptr(), xi.data_ptr(),
+                                       int(chi.numel()), float(lr),
+                                       loss.data_ptr() if loss is not None else None, _stream(stream)))
+
+    def gradients(self, proc: int, chi: torch.Tensor, u: torch.Tensor, xi: torch.Tensor, stream=None):
+        g = torch.zeros(self.NPARAM, dtype=torch.float32, device=chi.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=chi.device)
+        check(lib().qed_mlp_gradients(self.handle, proc, chi.data_ptr(), u.data_ptr(), xi.data_ptr(),
+                                      int(chi.numel()), g.data_ptr(), loss.data_ptr(), _stream(stream)))
+        return g, loss
+
+    def sample(self, proc: int, chi: torch.Tensor, u: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+        out = torch.empty_like(chi) if out is None else out
+        check(lib().qed_mlp_sample(self.handle, proc, chi.data_ptr(), u.data_ptr(), int(chi.numel()),
+                                   out.data_ptr(), _stream(stream)))
+        return out
+
+
+def qed_table_sample(t: Tables, proc: int, prec: int, chi: torch.Tensor, u: torch.Tensor,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Inverse-CDF samples through the 2-D tables (QS: xi; BW: the electron's fraction)."""
+    out = torch.empty_like(chi) if out is None else out
+    check(lib().qed_table_sample(t.handle, proc, prec, chi.data_ptr(), u.data_ptr(), int(chi.numel()),
+                                 out.data_ptr(), _stream(stream)))
+    return out
+
+
+def substep_opts_mlp(mlp: Mlp, photon_threshold=0.0, stats: Stats | None = None) -> SubstepOpts:
+    o = _opts(photon_threshold, stats)
+    o.sampler = 1
+    o.mlp = mlp.handle.value
+    return o

@@ -94,6 +94,108 @@ __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_b
     }
 }
 
+// One tile: THREADS x VEC consecutive particles of segment `sg` starting at
+// tile index `first`.  dry != 0 evaluates everything but stores nothing (used
+// by the launch-shape tuner).
+template <typename T, int VEC, int THREADS>
+__device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, long long first, const T *s_qs,
+                                            const T *s_bw, const TablesView<T> &tab, T dt, long long *stats,
+                                            int dry, int &bad)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t i0 = first * ((int64_t)THREADS * VEC) + (int64_t)threadIdx.x * VEC;
+
+    T px[VEC], py[VEC], pz[VEC], ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC], tau[VEC], tc[VEC];
+    const bool full = i0 + VEC <= n;
+    if (full) {
+        load_vec<T, VEC>(sg.px, i0, px);
+        load_vec<T, VEC>(sg.py, i0, py);
+        load_vec<T, VEC>(sg.pz, i0, pz);
+        load_vec<T, VEC>(sg.ex, i0, ex);
+        load_vec<T, VEC>(sg.ey, i0, ey);
+        load_vec<T, VEC>(sg.ez, i0, ez);
+        load_vec<T, VEC>(sg.bx, i0, bx);
+        load_vec<T, VEC>(sg.by, i0, by);
+        load_vec<T, VEC>(sg.bz, i0, bz);
+        load_vec<T, VEC>(sg.tau, i0, tau);
+        if constexpr (sizeof(T) == 4) load_vec<T, VEC>(sg.tau_c, i0, tc);
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const int64_t i = i0 + j;
+            const bool v = i < n;
+            px[j] = v ? sg.px[i] : T(0);
+            py[j] = v ? sg.py[i] : T(0);
+            pz[j] = v ? sg.pz[i] : T(0);
+            ex[j] = v ? sg.ex[i] : T(0);
+            ey[j] = v ? sg.ey[i] : T(0);
+            ez[j] = v ? sg.ez[i] : T(0);
+            bx[j] = v ? sg.bx[i] : T(0);
+            by[j] = v ? sg.by[i] : T(0);
+            bz[j] = v ? sg.bz[i] : T(0);
+            tau[j] = v ? sg.tau[i] : T(1);
+            if constexpr (sizeof(T) == 4) tc[j] = v ? sg.tau_c[i] : T(0);
+        }
+    }
+
+    bool fire[VEC];
+    T chi[VEC];
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        T c = sizeof(T) == 4 ? tc[j] : T(0);
+        fire[j] = evolve_one<T>(sg.proc, s_qs, s_bw, tab, px[j], py[j], pz[j], ex[j], ey[j], ez[j], bx[j], by[j],
+                                bz[j], dt, tau[j], c, chi[j], bad);
+        tc[j] = c;
+        fire[j] = fire[j] && (i0 + j < n);
+        cnt += fire[j] ? 1 : 0;
+    }
+    if (dry) return;
+
+    if (full) {
+        store_vec<T, VEC>(sg.tau, i0, tau);
+        if constexpr (sizeof(T) == 4) store_vec<T, VEC>(sg.tau_c, i0, tc);
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (i0 + j < n) {
+                sg.tau[i0 + j] = tau[j];
+                if constexpr (sizeof(T) == 4) sg.tau_c[i0 + j] = tc[j];
+            }
+        }
+    }
+
+    // warp-ballot compaction of the firing particles: one atomic per warp
+    if (__ballot_sync(0xffffffffu, cnt > 0)) {
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(sg.fire_count, (unsigned long long)wtot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        long long pos = (long long)base + incl - cnt;
+        int over = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (fire[j]) {
+                if (pos < sg.fire_cap) {
+                    sg.fire_idx[pos] = i0 + j;
+                    sg.fire_chi[pos] = (double)chi[j];
+                } else {
+                    ++over;
+                }
+                ++pos;
+            }
+        }
+        if (stats) warp_count(stats + QED_STAT_FIRE_OVERFLOW, over);
+    }
+}
+
+// segments as kernel parameters (a few species)
 template <typename T, int VEC, int MAXSEG>
 __global__ void __launch_bounds__(kEvolveThreads, 3)
     evolve_kernel(const __grid_constant__ EvolveArgs<T, MAXSEG> a)
@@ -102,6 +204,7 @@ __global__ void __launch_bounds__(kEvolveThreads, 3)
     __shared__ T s_bw[QED_MAX_TABLE_N];
     __shared__ long long s_end[MAXSEG];  // inclusive prefix of tile counts
     __shared__ long long s_n[MAXSEG];
+    constexpr int64_t tile = kEvolveTile<T, VEC>;
 
     for (int i = threadIdx.x; i < a.tab.qs_G.n; i += blockDim.x) s_qs[i] = a.tab.qs_G.ln_f[i];
     for (int i = threadIdx.x; i < a.tab.bw_T.n; i += blockDim.x) s_bw[i] = a.tab.bw_T.ln_f[i];
@@ -111,113 +214,122 @@ __global__ void __launch_bounds__(kEvolveThreads, 3)
             long long n = *a.seg[s].count;
             n = n < 0 ? 0 : (n > a.seg[s].capacity ? a.seg[s].capacity : n);
             s_n[s] = n;
-            acc += (n + kEvolveTile<T, VEC> - 1) / kEvolveTile<T, VEC>;
+            acc += (n + tile - 1) / tile;
             s_end[s] = acc;
         }
     }
     __syncthreads();
     const long long total = a.n_seg ? s_end[a.n_seg - 1] : 0;
-    const unsigned lane = threadIdx.x & 31u;
     int bad = 0;
-
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         int s = 0;
         while (t >= s_end[s]) ++s;
-        const EvolveSeg<T> &sg = a.seg[s];
-        const long long first = t - (s ? s_end[s - 1] : 0);
-        const int64_t n = s_n[s];
-        const int64_t i0 = first * kEvolveTile<T, VEC> + (int64_t)threadIdx.x * VEC;
-
-        T px[VEC], py[VEC], pz[VEC], ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC], tau[VEC], tc[VEC];
-        const bool full = i0 + VEC <= n;
-        if (full) {
-            load_vec<T, VEC>(sg.px, i0, px);
-            load_vec<T, VEC>(sg.py, i0, py);
-            load_vec<T, VEC>(sg.pz, i0, pz);
-            load_vec<T, VEC>(sg.ex, i0, ex);
-            load_vec<T, VEC>(sg.ey, i0, ey);
-            load_vec<T, VEC>(sg.ez, i0, ez);
-            load_vec<T, VEC>(sg.bx, i0, bx);
-            load_vec<T, VEC>(sg.by, i0, by);
-            load_vec<T, VEC>(sg.bz, i0, bz);
-            load_vec<T, VEC>(sg.tau, i0, tau);
-            if constexpr (sizeof(T) == 4) load_vec<T, VEC>(sg.tau_c, i0, tc);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                const int64_t i = i0 + j;
-                const bool v = i < n;
-                px[j] = v ? sg.px[i] : T(0);
-                py[j] = v ? sg.py[i] : T(0);
-                pz[j] = v ? sg.pz[i] : T(0);
-                ex[j] = v ? sg.ex[i] : T(0);
-                ey[j] = v ? sg.ey[i] : T(0);
-                ez[j] = v ? sg.ez[i] : T(0);
-                bx[j] = v ? sg.bx[i] : T(0);
-                by[j] = v ? sg.by[i] : T(0);
-                bz[j] = v ? sg.bz[i] : T(0);
-                tau[j] = v ? sg.tau[i] : T(1);
-                if constexpr (sizeof(T) == 4) tc[j] = v ? sg.tau_c[i] : T(0);
-            }
-        }
-
-        bool fire[VEC];
-        T chi[VEC];
-        int cnt = 0;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            T c = sizeof(T) == 4 ? tc[j] : T(0);
-            fire[j] = evolve_one<T>(sg.proc, s_qs, s_bw, a.tab, px[j], py[j], pz[j], ex[j], ey[j], ez[j], bx[j],
-                                    by[j], bz[j], a.dt, tau[j], c, chi[j], bad);
-            tc[j] = c;
-            fire[j] = fire[j] && (i0 + j < n);
-            cnt += fire[j] ? 1 : 0;
-        }
-
-        if (full) {
-            store_vec<T, VEC>(sg.tau, i0, tau);
-            if constexpr (sizeof(T) == 4) store_vec<T, VEC>(sg.tau_c, i0, tc);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                if (i0 + j < n) {
-                    sg.tau[i0 + j] = tau[j];
-                    if constexpr (sizeof(T) == 4) sg.tau_c[i0 + j] = tc[j];
-                }
-            }
-        }
-
-        // warp-ballot compaction of the firing particles: one atomic per warp
-        if (__ballot_sync(0xffffffffu, cnt > 0)) {
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)lane >= o) incl += v;
-            }
-            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-            unsigned long long base = 0;
-            if (lane == 31) base = atomicAdd(sg.fire_count, (unsigned long long)wtot);
-            base = __shfl_sync(0xffffffffu, base, 31);
-            long long pos = (long long)base + incl - cnt;
-            int over = 0;
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                if (fire[j]) {
-                    if (pos < sg.fire_cap) {
-                        sg.fire_idx[pos] = i0 + j;
-                        sg.fire_chi[pos] = (double)chi[j];
-                    } else {
-                        ++over;
-                    }
-                    ++pos;
-                }
-            }
-            if (a.stats) warp_count(a.stats + QED_STAT_FIRE_OVERFLOW, over);
-        }
+        evolve_tile<T, VEC, kEvolveThreads>(a.seg[s], s_n[s], t - (s ? s_end[s - 1] : 0), s_qs, s_bw, a.tab, a.dt,
+                                            a.stats, 0, bad);
     }
     if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
 }
+
+// Segments in device memory (many patches): every CTA reads all segment
+// counts, forms the prefix sum of their tile counts in shared memory (a block
+// scan), and strides over the combined tile space; a tile's segment is found
+// by binary search.
+template <typename T, int VEC, int THREADS>
+__global__ void __launch_bounds__(THREADS, 768 / THREADS)
+    evolve_seg_kernel(const EvolveSeg<T> *__restrict__ segs, int n_seg, TablesView<T> tab, T dt, long long *stats,
+                      int dry)
+{
+    __shared__ T s_qs[QED_MAX_TABLE_N];
+    __shared__ T s_bw[QED_MAX_TABLE_N];
+    __shared__ long long s_warp[THREADS / 32];
+    extern __shared__ long long s_dyn[];  // [n_seg] inclusive tile prefix, [n_seg] counts
+    long long *s_end = s_dyn, *s_n = s_dyn + n_seg;
+    constexpr int64_t tile = (int64_t)THREADS * VEC;
+
+    for (int i = threadIdx.x; i < tab.qs_G.n; i += THREADS) s_qs[i] = tab.qs_G.ln_f[i];
+    for (int i = threadIdx.x; i < tab.bw_T.n; i += THREADS) s_bw[i] = tab.bw_T.ln_f[i];
+    // block scan: thread k owns segments [k*per, (k+1)*per)
+    const int per = (n_seg + THREADS - 1) / THREADS;
+    const int s0 = threadIdx.x * per, s1 = min(n_seg, s0 + per);
+    long long local = 0;
+    for (int s = s0; s < s1; ++s) {
+        long long n = *segs[s].count;
+        n = n < 0 ? 0 : (n > segs[s].capacity ? segs[s].capacity : n);
+        s_n[s] = n;
+        local += (n + tile - 1) / tile;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    long long woff = 0;
+    for (int w = 0; w < warp; ++w) woff += s_warp[w];
+    long long acc = woff + incl - local;
+    for (int s = s0; s < s1; ++s) {
+        acc += (s_n[s] + tile - 1) / tile;
+        s_end[s] = acc;
+    }
+    __syncthreads();
+    const long long total = n_seg ? s_end[n_seg - 1] : 0;
+    int bad = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n_seg - 1;  // first s with s_end[s] > t
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_end[mid] > t)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        evolve_tile<T, VEC, THREADS>(segs[lo], s_n[lo], t - (lo ? s_end[lo - 1] : 0), s_qs, s_bw, tab, dt, stats,
+                                     dry, bad);
+    }
+    if (stats && !dry) warp_count(stats + QED_STAT_NONFINITE, bad);
+}
+
+template <typename T, int THREADS>
+static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const TablesView<T> &tab, T dt,
+                                  long long *stats, int dry, bool vec, int ctas_per_sm, cudaStream_t st)
+{
+    const size_t dyn = (size_t)n_seg * 2 * sizeof(long long);
+    int grid = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 768 / THREADS);
+    if (vec) {
+        constexpr int V = sizeof(T) == 4 ? 4 : 2;
+        if (dyn > 48 * 1024)
+            QED_CUDA_TRY(cudaFuncSetAttribute(evolve_seg_kernel<T, V, THREADS>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        evolve_seg_kernel<T, V, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
+    } else {
+        if (dyn > 48 * 1024)
+            QED_CUDA_TRY(cudaFuncSetAttribute(evolve_seg_kernel<T, 1, THREADS>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        evolve_seg_kernel<T, 1, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
+    }
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+template <typename T>
+qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt,
+                                  long long *stats, int dry, bool vec, int threads, int ctas_per_sm, cudaStream_t st)
+{
+    if (n_seg <= 0) return QED_OK;
+    switch (threads) {
+    case 128: return launch_seg_impl<T, 128>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
+    case 512: return launch_seg_impl<T, 512>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
+    default: return launch_seg_impl<T, 256>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
+    }
+}
+
+template qed_status launch_evolve_segments<float>(const EvolveSeg<float> *, int, const TablesView<float> &, float,
+                                                  long long *, int, bool, int, int, cudaStream_t);
+template qed_status launch_evolve_segments<double>(const EvolveSeg<double> *, int, const TablesView<double> &,
+                                                   double, long long *, int, bool, int, int, cudaStream_t);
 
 // clamp the firing counters to their capacity once the evolution is done
 __global__ void clamp_fire_counts(unsigned long long *c0, int64_t cap0, unsigned long long *c1, int64_t cap1,

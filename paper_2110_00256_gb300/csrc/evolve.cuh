@@ -47,6 +47,12 @@ qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t ca
 template <typename T>
 bool fill_seg(EvolveSeg<T> &g, const qed_species *sp, int proc, const qed_fire_list *fire);
 
+// segments in device memory (the batched substep); threads in {128, 256, 512},
+// ctas_per_sm 0 = as many as the register budget allows; dry != 0 stores nothing
+template <typename T>
+qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt,
+                                  long long *stats, int dry, bool vec, int threads, int ctas_per_sm, cudaStream_t st);
+
 qed_status check_fire(const qed_fire_list *f, const char *name);
 
 __global__ void clamp_fire_counts(unsigned long long *c0, int64_t cap0, unsigned long long *c1, int64_t cap1,

@@ -1,0 +1,444 @@
+// mlp.cu -- the learned sampler's object, training (forward + backward on the
+// CUDA cores in FP32 with the same bf16 rounding as inference, Adam), batch
+// inference on the tensor cores, and batch sampling through the 2-D tables for
+// comparison.
+#include <cmath>
+#include <cstring>
+
+#include "mlp.cuh"
+#include "physics.cuh"
+
+namespace qed {
+
+MlpView mlp_view(const qed_mlp *m, int proc)
+{
+    MlpView v;
+    v.w = m->w[proc];
+    v.ln_min = (float)std::log(m->chi_min[proc]);
+    v.scale = (float)(2.0 / (std::log(m->chi_max[proc]) - std::log(m->chi_min[proc])));
+    v.chi_min = (float)m->chi_min[proc];
+    v.chi_max = (float)m->chi_max[proc];
+    v.proc = proc;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// initialisation: Glorot-uniform weights from Philox, zero biases
+// ---------------------------------------------------------------------------
+__global__ void mlp_init_kernel(float *p, uint64_t seed, int proc)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x) {
+        float a = 0.f;
+        if (i < kOffB1)
+            a = sqrtf(6.f / (2 + kMlpH));
+        else if (i >= kOffW2 && i < kOffB2)
+            a = sqrtf(6.f / (kMlpH + kMlpH));
+        else if (i >= kOffW3 && i < kOffB3)
+            a = sqrtf(6.f / (kMlpH + 1));
+        const U4 w = draw(seed, (uint64_t)proc * 1000003ull + (uint64_t)i, 0, 5u);
+        const float u = (float)uniform53(w.x, w.y);
+        p[i] = a * (2.f * u - 1.f);
+    }
+}
+
+__global__ void mlp_to_bf16_kernel(const float *p, __nv_bfloat16 *w)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x)
+        w[i] = __float2bfloat16_rn(p[i]);
+}
+
+// ---------------------------------------------------------------------------
+// training: one CTA of kTrainThreads threads takes kTrainThreads samples at a
+// time (one per thread) and accumulates the gradient of the mean squared error
+// in shared memory; one atomic flush per CTA at the end.
+// ---------------------------------------------------------------------------
+constexpr int kTrainThreads = 128;
+constexpr int kTS = kTrainThreads + 1;  // padded sample stride of the [64][samples] buffers
+
+struct TrainSmem {
+    float w1[kMlpH * 2], b1[kMlpH], w2[kMlpH * kMlpH], b2[kMlpH], w3[kMlpH], b3;
+    float g[kMlpParams];       // gradient accumulator of this CTA
+    float h1[kMlpH * kTS];     // bf16-rounded h1, [k][s]
+    float z2[kMlpH * kTS];     // z2, then d2 = dL/dz2
+    float q[kMlpH * kTS];      // dy * h2, then d1 = dL/dz1
+    float x[2][kTrainThreads], dy[kTrainThreads];
+    float loss;
+};
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, const double *__restrict__ chi,
+                                                                    const double *__restrict__ uu,
+                                                                    const double *__restrict__ xi, int64_t n,
+                                                                    float *grad, float *loss_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kMlpH * 2; i += blockDim.x) S.w1[i] = __bfloat162float(v.w[kOffW1 + i]);
+    for (int i = tid; i < kMlpH * kMlpH; i += blockDim.x) S.w2[i] = __bfloat162float(v.w[kOffW2 + i]);
+    for (int i = tid; i < kMlpH; i += blockDim.x) {
+        S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
+        S.b2[i] = __bfloat162float(v.w[kOffB2 + i]);
+        S.w3[i] = __bfloat162float(v.w[kOffW3 + i]);
+    }
+    for (int i = tid; i < kMlpParams; i += blockDim.x) S.g[i] = 0.f;
+    if (tid == 0) {
+        S.b3 = __bfloat162float(v.w[kOffB3]);
+        S.loss = 0.f;
+    }
+    __syncthreads();
+    const float inv_n = 1.0f / (float)n;
+    float my_loss = 0.f;
+
+    for (int64_t base = (int64_t)blockIdx.x * kTrainThreads; base < n; base += (int64_t)gridDim.x * kTrainThreads) {
+        const int64_t i = base + tid;
+        const bool valid = i < n;
+        float x1 = 0.f, x2 = 0.f, tgt = 0.f;
+        if (valid) {
+            mlp_features(v, chi[i], uu[i], x1, x2);
+            if (v.proc == QED_PROC_QS) {
+                tgt = (float)(log(xi[i]) - 3.0 * log(uu[i]));
+            } else {
+                const double xm = xi[i];
+                tgt = (float)(uu[i] <= 0.5 ? xm : 1.0 - xm);  // folded fraction of the sampled lepton
+            }
+        }
+        S.x[0][tid] = x1;
+        S.x[1][tid] = x2;
+        // forward
+        for (int k = 0; k < kMlpH; ++k)
+            S.h1[k * kTS + tid] = bf16r(gelu(fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k]))));
+        float y = S.b3;
+        for (int j = 0; j < kMlpH; ++j) {
+            float z = S.b2[j];
+            for (int k = 0; k < kMlpH; ++k) z = fmaf(S.w2[j * kMlpH + k], S.h1[k * kTS + tid], z);
+            S.z2[j * kTS + tid] = z;
+            y = fmaf(S.w3[j], gelu(z), y);
+        }
+        const float r = valid ? y - tgt : 0.f;
+        my_loss += r * r;
+        const float dy = 2.f * r * inv_n;
+        S.dy[tid] = dy;
+        for (int j = 0; j < kMlpH; ++j) {
+            const float z = S.z2[j * kTS + tid];
+            S.q[j * kTS + tid] = dy * gelu(z);                    // for dW3
+            S.z2[j * kTS + tid] = dy * S.w3[j] * gelu_grad(z);    // d2
+        }
+        __syncthreads();
+        // dW2 = d2^T h1, db2 = sum d2, dW3 = sum dy h2, db3 = sum dy
+        for (int e = tid; e < kMlpH * kMlpH; e += blockDim.x) {
+            const int j = e / kMlpH, k = e % kMlpH;
+            float acc = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) acc = fmaf(S.z2[j * kTS + s], S.h1[k * kTS + s], acc);
+            S.g[kOffW2 + e] += acc;
+        }
+        if (tid < kMlpH) {
+            float a = 0.f, b = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) {
+                a += S.z2[tid * kTS + s];
+                b += S.q[tid * kTS + s];
+            }
+            S.g[kOffB2 + tid] += a;
+            S.g[kOffW3 + tid] += b;
+        } else if (tid == kMlpH) {
+            float a = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) a += S.dy[s];
+            S.g[kOffB3] += a;
+        }
+        __syncthreads();
+        // d1 = (W2^T d2) * gelu'(z1), per sample
+        for (int k = 0; k < kMlpH; ++k) {
+            float acc = 0.f;
+            for (int j = 0; j < kMlpH; ++j) acc = fmaf(S.w2[j * kMlpH + k], S.z2[j * kTS + tid], acc);
+            const float z1 = fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k]));
+            S.q[k * kTS + tid] = acc * gelu_grad(z1);
+        }
+        __syncthreads();
+        // dW1 = d1^T x, db1 = sum d1
+        if (tid < kMlpH) {
+            float a0 = 0.f, a1 = 0.f, b = 0.f;
+            for (int s = 0; s < kTrainThreads; ++s) {
+                const float d = S.q[tid * kTS + s];
+                a0 = fmaf(d, S.x[0][s], a0);
+                a1 = fmaf(d, S.x[1][s], a1);
+                b += d;
+            }
+            S.g[kOffW1 + 2 * tid] += a0;
+            S.g[kOffW1 + 2 * tid + 1] += a1;
+            S.g[kOffB1 + tid] += b;
+        }
+        __syncthreads();
+    }
+    atomicAdd(&S.loss, my_loss);
+    __syncthreads();
+    for (int i = tid; i < kMlpParams; i += blockDim.x) atomicAdd(grad + i, S.g[i]);
+    if (tid == 0) atomicAdd(loss_out, S.loss * inv_n);
+}
+
+// Adam (Kingma & Ba 2015); refreshes the bf16 copy and clears the gradient
+__global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfloat16 *w, float lr, float bc1,
+                                float bc2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+        p[i] = pi;
+        w[i] = __float2bfloat16_rn(pi);
+        g[i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batch inference on the tensor cores: each warp evaluates 32 samples
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kInferThreads) mlp_sample_kernel(MlpView v, const double *__restrict__ chi,
+                                                                     const double *__restrict__ uu, int64_t n,
+                                                                     double *__restrict__ xi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
+    mlp_stage(S.net, v.w);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * kInferWarps + warp, nw = (int64_t)gridDim.x * kInferWarps;
+    for (int64_t base = gw * 32; base < n; base += nw * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        const double c = valid ? chi[i] : 1.0, u = valid ? uu[i] : 0.5;
+        float x1, x2;
+        mlp_features(v, c, u, x1, x2);
+        const float y = mlp_forward_warp(S.net, S.h1[warp], S.y[warp], x1, x2);
+        if (valid) xi[i] = mlp_output(v.proc, y, u);
+    }
+}
+
+// batch inverse-CDF sampling through the 2-D tables (the path the network replaces)
+template <typename T>
+__global__ void table_sample_kernel(Table2D<T> tb, int proc, const double *__restrict__ chi,
+                                    const double *__restrict__ uu, int64_t n, double *__restrict__ xi)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double u = uu[i];
+        if (proc == QED_PROC_QS) {
+            xi[i] = (double)qs_sample_xi<T>(tb, (T)chi[i], sample_uniform<T>(u));
+        } else {
+            bool electron;
+            const T xs = bw_sample_xi<T>(tb, (T)chi[i], u, electron);
+            xi[i] = electron ? (double)xs : 1.0 - (double)xs;
+        }
+    }
+}
+
+int sm_count();
+
+static qed_status check_mlp(const qed_mlp *m, int proc)
+{
+    if (!m) QED_FAIL(QED_ERR_INVALID_ARG, "mlp handle is NULL");
+    if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", proc);
+    return QED_OK;
+}
+
+size_t infer_smem_bytes() { return sizeof(InferSmem); }
+
+}  // namespace qed
+
+using namespace qed;
+
+static void free_mlp(qed_mlp *m)
+{
+    if (!m) return;
+    for (int p = 0; p < 2; ++p) {
+        void *ptrs[] = {m->master[p], m->adam_m[p], m->adam_v[p], m->grad[p], m->loss[p], m->w[p]};
+        for (void *x : ptrs)
+            if (x) cudaFree(x);
+    }
+    delete m;
+}
+
+extern "C" qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp **out, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if (!out) QED_FAIL(QED_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if ((s = check_tables(t))) return s;
+    qed_mlp *m = new qed_mlp();
+    memset(m, 0, sizeof(*m));
+    cudaGetDevice(&m->device);
+    m->chi_min[0] = t->params.qs.chi_min, m->chi_max[0] = t->params.qs.chi_max;
+    m->chi_min[1] = t->params.bw.chi_min, m->chi_max[1] = t->params.bw.chi_max;
+    cudaStream_t st = as_stream(stream);
+    for (int p = 0; p < 2; ++p) {
+        cudaError_t e = cudaSuccess;
+        float **fp[] = {&m->master[p], &m->adam_m[p], &m->adam_v[p], &m->grad[p]};
+        for (float **f : fp)
+            if (e == cudaSuccess) e = cudaMalloc((void **)f, kMlpParams * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&m->loss[p], sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&m->w[p], kMlpParams * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_m[p], 0, kMlpParams * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_v[p], 0, kMlpParams * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->grad[p], 0, kMlpParams * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->loss[p], 0, sizeof(float), st);
+        if (e != cudaSuccess) {
+            free_mlp(m);
+            QED_FAIL(QED_ERR_CUDA, "mlp allocation failed: %s", cudaGetErrorString(e));
+        }
+        mlp_init_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m->master[p], seed, p);
+        mlp_to_bf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m->master[p], m->w[p]);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_mlp(m);
+        QED_FAIL(QED_ERR_CUDA, "mlp initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_destroy(qed_mlp *m)
+{
+    clear_error();
+    free_mlp(m);
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_get_params(const qed_mlp *m, qed_process proc, float *host_params)
+{
+    clear_error();
+    qed_status s = check_mlp(m, proc);
+    if (s) return s;
+    if (!host_params) QED_FAIL(QED_ERR_INVALID_ARG, "host_params is NULL");
+    QED_CUDA_TRY(cudaMemcpy(host_params, m->master[proc], kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_set_params(qed_mlp *m, qed_process proc, const float *host_params, void *stream)
+{
+    clear_error();
+    qed_status s = check_mlp(m, proc);
+    if (s) return s;
+    if (!host_params) QED_FAIL(QED_ERR_INVALID_ARG, "host_params is NULL");
+    cudaStream_t st = as_stream(stream);
+    QED_CUDA_TRY(cudaMemcpyAsync(m->master[proc], host_params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, st));
+    mlp_to_bf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m->master[proc], m->w[proc]);
+    QED_LAUNCH_CHECK();
+    QED_CUDA_TRY(cudaMemsetAsync(m->adam_m[proc], 0, kMlpParams * sizeof(float), st));
+    QED_CUDA_TRY(cudaMemsetAsync(m->adam_v[proc], 0, kMlpParams * sizeof(float), st));
+    QED_CUDA_TRY(cudaStreamSynchronize(st));
+    m->step[proc] = 0;
+    return QED_OK;
+}
+
+static qed_status launch_train(qed_mlp *m, int proc, const double *chi, const double *u, const double *xi, int64_t n,
+                               cudaStream_t st)
+{
+    static bool attr = false;
+    const size_t sm = sizeof(TrainSmem);
+    if (!attr) {
+        QED_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    QED_CUDA_TRY(cudaMemsetAsync(m->loss[proc], 0, sizeof(float), st));
+    int64_t blocks = (n + kTrainThreads - 1) / kTrainThreads;
+    const int64_t cap = (int64_t)sm_count();
+    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+    mlp_train_kernel<<<(int)blocks, kTrainThreads, sm, st>>>(mlp_view(m, proc), chi, u, xi, n, m->grad[proc],
+                                                             m->loss[proc]);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+static qed_status check_batch(const double *chi, const double *u, const double *xi, int64_t n)
+{
+    if (n <= 0) QED_FAIL(QED_ERR_INVALID_ARG, "batch size must be positive");
+    if (!chi || !u || !xi) QED_FAIL(QED_ERR_INVALID_ARG, "a batch array is NULL");
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_gradients(qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                                        const double *d_xi, int64_t n, float *d_grad, float *d_loss, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_mlp(m, proc))) return s;
+    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    if (!d_grad) QED_FAIL(QED_ERR_INVALID_ARG, "d_grad is NULL");
+    cudaStream_t st = as_stream(stream);
+    QED_CUDA_TRY(cudaMemsetAsync(m->grad[proc], 0, kMlpParams * sizeof(float), st));
+    if ((s = launch_train(m, proc, d_chi, d_u, d_xi, n, st))) return s;
+    QED_CUDA_TRY(cudaMemcpyAsync(d_grad, m->grad[proc], kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (d_loss) QED_CUDA_TRY(cudaMemcpyAsync(d_loss, m->loss[proc], sizeof(float), cudaMemcpyDeviceToDevice, st));
+    QED_CUDA_TRY(cudaMemsetAsync(m->grad[proc], 0, kMlpParams * sizeof(float), st));
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_train_step(qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                                         const double *d_xi, int64_t n, float lr, float *d_loss, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_mlp(m, proc))) return s;
+    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    if (!(lr > 0.f)) QED_FAIL(QED_ERR_INVALID_ARG, "learning rate must be positive");
+    cudaStream_t st = as_stream(stream);
+    if ((s = launch_train(m, proc, d_chi, d_u, d_xi, n, st))) return s;
+    const int64_t k = ++m->step[proc];
+    const float bc1 = 1.f - powf(0.9f, (float)k), bc2 = 1.f - powf(0.999f, (float)k);
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m->master[proc], m->adam_m[proc], m->adam_v[proc],
+                                                              m->grad[proc], m->w[proc], lr, bc1, bc2);
+    QED_LAUNCH_CHECK();
+    if (d_loss) QED_CUDA_TRY(cudaMemcpyAsync(d_loss, m->loss[proc], sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
+                                     int64_t n, double *d_xi, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_mlp(m, proc))) return s;
+    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    static bool attr = false;
+    const size_t sm = sizeof(InferSmem);
+    if (!attr) {
+        QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    int64_t blocks = (n + kInferThreads - 1) / kInferThreads;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+    mlp_sample_kernel<<<(int)blocks, kInferThreads, sm, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n, d_xi);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+extern "C" qed_status qed_table_sample(const qed_tables *t, qed_process proc, qed_precision prec, const double *d_chi,
+                                       const double *d_u, int64_t n, double *d_xi, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_tables(t))) return s;
+    if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", (int)proc);
+    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+    cudaStream_t st = as_stream(stream);
+    if (prec == QED_F32) {
+        TablesView<float> v = make_view<float>(t);
+        table_sample_kernel<float><<<(int)blocks, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
+                                                                d_u, n, d_xi);
+    } else {
+        TablesView<double> v = make_view<double>(t);
+        table_sample_kernel<double><<<(int)blocks, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
+                                                                 d_u, n, d_xi);
+    }
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}

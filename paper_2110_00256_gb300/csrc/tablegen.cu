@@ -28,8 +28,8 @@ qed_status alloc_tables(const qed_table_params *p, qed_tables **out);
 qed_status finish_tables(qed_tables *t, cudaStream_t st);
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kTsStep = 0.125;  // tanh-sinh step
-constexpr int kTsHalf = 26;        // nodes k = -26..26 (|k h| <= 3.25)
+constexpr double kTsStep = 1.0 / 16.0;  // tanh-sinh step
+constexpr int kTsHalf = 52;             // nodes k = -52..52 (|k h| <= 3.25)
 constexpr double kQsBelow = 100.0;  // the QS integral below xi_min starts at xi_min e^{-100}
 
 // e^x int_x^inf K_a and e^x K_b, trapezoid rule in t

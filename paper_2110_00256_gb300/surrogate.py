@@ -1,0 +1,89 @@
+"""Training and evaluation of the learned inverse-CDF sampler on the GPU.
+
+Training data: (chi, U, xi) with chi log-uniform over the table range, U uniform
+in (0, 1) (both from a seeded torch generator on the device), and xi the FP64
+inverse-CDF sample of the same (chi, U) through a fine FP64 table made by
+qed_tables_generate (the table generator is the reference the network learns).
+Every step of the training runs in libqed's kernels (forward, backward, Adam).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import api
+
+
+def make_data(tables: api.Tables, proc: int, n: int, seed: int, device="cuda"):
+    """n training samples (chi, U, xi) on the device."""
+    p = tables.params
+    ax = p.qs if proc == api.QED_PROC_QS else p.bw
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
+    chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device=device, dtype=torch.float64))
+    u = torch.rand(n, generator=g, device=device, dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
+    xi = api.qed_table_sample(tables, proc, api.QED_F64, chi, u)
+    return chi, u, xi
+
+
+def train(mlp: api.Mlp, data_tables: api.Tables, proc: int, n_samples: int = 10_000_000, epochs: int = 6,
+          batch: int = 65536, lr: float = 3e-3, lr_final: float = 1e-4, seed: int = 1, log_every: int = 0):
+    """Train one network; returns the loss history (one value per logged step)."""
+    chi, u, xi = make_data(data_tables, proc, n_samples, seed)
+    g = torch.Generator(device=chi.device)
+    g.manual_seed(seed + 1)
+    steps = epochs * ((n_samples + batch - 1) // batch)
+    loss = torch.zeros(1, dtype=torch.float32, device=chi.device)
+    hist = []
+    k = 0
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        perm = torch.randperm(n_samples, generator=g, device=chi.device)
+        c, uu, x = chi[perm], u[perm], xi[perm]
+        for b in range(0, n_samples, batch):
+            e = min(b + batch, n_samples)
+            # cosine decay from lr to lr_final
+            rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * k / max(steps - 1, 1)))
+            mlp.train_step(proc, c[b:e], uu[b:e], x[b:e], rate, loss)
+            k += 1
+            if log_every and k % log_every == 0:
+                hist.append(float(loss.item()))
+    torch.cuda.synchronize()
+    return {"steps": k, "seconds": time.perf_counter() - t0, "final_loss": float(loss.item()), "history": hist}
+
+
+def ks_distance(a: torch.Tensor, b: torch.Tensor) -> float:
+    """Two-sample Kolmogorov-Smirnov distance between two sets of samples."""
+    x = torch.sort(a.double()).values
+    y = torch.sort(b.double()).values
+    allv = torch.cat([x, y])
+    fa = torch.searchsorted(x, allv, right=True).double() / x.numel()
+    fb = torch.searchsorted(y, allv, right=True).double() / y.numel()
+    return float((fa - fb).abs().max().item())
+
+
+def compare(mlp: api.Mlp, tables: api.Tables, proc: int, n: int = 1_000_000, seed: int = 99, bins: int = 5,
+            prec: int = api.QED_F32):
+    """KS distance between network samples and table samples of the same (chi, U),
+    overall and in log-chi bins; also the KS of the per-bin xi distributions."""
+    p = tables.params
+    ax = p.qs if proc == api.QED_PROC_QS else p.bw
+    gdev = torch.Generator(device="cuda")
+    gdev.manual_seed(seed)
+    lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
+    t = torch.rand(n, generator=gdev, device="cuda", dtype=torch.float64)
+    chi = torch.exp(lo + (hi - lo) * t)
+    u = torch.rand(n, generator=gdev, device="cuda", dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
+    xm = mlp.sample(proc, chi, u)
+    xt = api.qed_table_sample(tables, proc, prec, chi, u)
+    key = (lambda v: torch.log(v)) if proc == api.QED_PROC_QS else (lambda v: v)
+    out = {"overall": ks_distance(key(xm), key(xt)), "bins": []}
+    edges = torch.linspace(0, 1, bins + 1, dtype=torch.float64)
+    for i in range(bins):
+        m = (t >= edges[i].item()) & (t < edges[i + 1].item())
+        out["bins"].append(ks_distance(key(xm[m]), key(xt[m])))
+    return out

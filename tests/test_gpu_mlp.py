@@ -1,0 +1,134 @@
+"""The learned sampler on the GPU against its FP64 reference (oracle/mlp.py):
+forward pass (tensor-core inference), gradients of the training kernel,
+training progress, agreement of the trained network with the tables (KS), and
+the substep running with the learned sampler."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2110_00256_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def tables(api):
+    return api.qed_tables_generate(api.table_params(qs_n_chi=128, qs_n_xi=128, bw_n_chi=128, bw_n_xi=128))
+
+
+def _ranges(api, tables, proc):
+    p = tables.params
+    ax = p.qs if proc == 0 else p.bw
+    return ax.chi_min, ax.chi_max
+
+
+def _batch(api, tables, proc, n, seed):
+    lo, hi = (math.log(v) for v in _ranges(api, tables, proc))
+    r = np.random.default_rng(seed)
+    chi = np.exp(r.uniform(lo - 0.5, hi + 0.5, n))  # a little outside the range too (clamped)
+    u = r.uniform(1e-9, 1 - 1e-9, n)
+    return chi, u
+
+
+@pytest.mark.parametrize("proc", [0, 1])
+def test_forward_matches_oracle(api, tables, proc):
+    m = api.Mlp(tables, seed=5 + proc)
+    theta = m.get_params(proc).astype(np.float64)
+    chi, u = _batch(api, tables, proc, 20000, 3 + proc)
+    xi = m.sample(proc, torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
+    cmin, cmax = _ranges(api, tables, proc)
+    X = omlp.features(proc, chi, u, cmin, cmax)
+    y_ref, _ = omlp.forward(theta, X, round_bf16=True)
+    if proc == 0:
+        y_gpu = np.log(xi) - 3 * np.log(u)
+        ok = y_ref + 3 * np.log(u) < -1e-3  # outside the clamp at xi = 1
+    else:
+        xs = np.where(u <= 0.5, xi, 1 - xi)
+        y_gpu = xs
+        ok = (y_ref > 1e-3) & (y_ref < 0.5 - 1e-3)
+    d = np.abs(y_gpu[ok] - y_ref[ok])
+    # tanh.approx (|rel err| < 2^-10.99) and bf16 ties of h1 that flip between the
+    # FP32 and FP64 evaluations bound the difference
+    assert ok.sum() > 1000
+    assert np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
+
+
+@pytest.mark.parametrize("proc", [0, 1])
+def test_gradients_match_oracle(api, tables, proc):
+    m = api.Mlp(tables, seed=11 + proc)
+    theta = m.get_params(proc).astype(np.float64)
+    n = 4096
+    chi, u = _batch(api, tables, proc, n, 21 + proc)
+    dev = {k: torch.tensor(v, device="cuda") for k, v in (("chi", chi), ("u", u))}
+    xi = api.qed_table_sample(tables, proc, api.QED_F64, dev["chi"], dev["u"])
+    g, loss = m.gradients(proc, dev["chi"], dev["u"], xi)
+    g = g.cpu().numpy().astype(np.float64)
+    cmin, cmax = _ranges(api, tables, proc)
+    X = omlp.features(proc, chi, u, cmin, cmax)
+    t = omlp.targets(proc, u, xi.cpu().numpy()) if proc == 0 else \
+        np.where(u <= 0.5, xi.cpu().numpy(), 1 - xi.cpu().numpy())
+    l_ref, g_ref = omlp.loss_and_grad(theta, X, t, round_bf16=True)
+    assert float(loss.item()) == pytest.approx(l_ref, rel=1e-2)
+    segs = {"W1": (0, 128), "b1": (128, 192), "W2": (192, 4288), "b2": (4288, 4352), "W3": (4352, 4416),
+            "b3": (4416, 4417)}
+    for name, (a, b) in segs.items():
+        rel = np.linalg.norm(g[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-12)
+        assert rel < 2e-2, (name, rel)
+
+
+@pytest.mark.parametrize("proc", [0, 1])
+def test_training_learns_the_tables(api, tables, proc):
+    from paper_2110_00256_gb300 import surrogate
+    fine = api.qed_tables_generate(api.table_params(qs_n_chi=256, qs_n_xi=512, bw_n_chi=256, bw_n_xi=512))
+    m = api.Mlp(fine, seed=31 + proc)
+    before = surrogate.compare(m, fine, proc, n=200_000, prec=api.QED_F64)["overall"]
+    rep = surrogate.train(m, fine, proc, n_samples=1_000_000, epochs=8, batch=32768, log_every=10)
+    h = rep["history"]
+    assert h[-1] < 0.2 * h[0]
+    after = surrogate.compare(m, fine, proc, n=200_000, prec=api.QED_F64)
+    assert after["overall"] < 0.5 * before and after["overall"] < 0.05, (before, after)
+
+
+def test_substep_with_learned_sampler(api, tables):
+    from paper_2110_00256_gb300 import workloads
+    m = api.Mlp(tables, seed=41)
+    n = 20000
+    host = {"electrons": workloads.paper_benchmark(n, 1, 0), "positrons": workloads.paper_benchmark(n, 2, 10 ** 12),
+            "photons": workloads.paper_benchmark(n, 3, 2 * 10 ** 12)}
+    for v in host.values():
+        v["tau"] *= 1e-3
+    bufs = {k: api.SpeciesBuffers(3 * n, api.QED_F64).set(v) for k, v in host.items()}
+    fire = [api.FireBuffers(3 * n) for _ in range(3)]
+    st = api.Stats()
+    api.qed_substep(tables, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 4, 0, fire, stats=st,
+                    mlp=m)
+    torch.cuda.synchronize()
+    s = st.as_dict()
+    assert s["qs_events"] > 100 and s["pairs"] > 10 and s["dropped_capacity"] == 0
+
+    def energy(d):
+        e = 0.0
+        for k in ("electrons", "positrons"):
+            x = d[k]
+            e += np.sum(x["weight"] * np.sqrt(1 + x["px"] ** 2 + x["py"] ** 2 + x["pz"] ** 2))
+        x = d["photons"]
+        return e + np.sum(x["weight"] * np.sqrt(x["px"] ** 2 + x["py"] ** 2 + x["pz"] ** 2))
+
+    got = {k: b.to_host() for k, b in bufs.items()}
+    assert energy(got) == pytest.approx(energy(host), rel=1e-12)
+    # the firing decisions do not depend on the sampler: same counts as the table path
+    bufs2 = {k: api.SpeciesBuffers(3 * n, api.QED_F64).set(v) for k, v in host.items()}
+    st2 = api.Stats()
+    api.qed_substep(tables, bufs2["electrons"], bufs2["positrons"], bufs2["photons"], 10.0, 4, 0,
+                    [api.FireBuffers(3 * n) for _ in range(3)], stats=st2)
+    torch.cuda.synchronize()
+    assert st2.as_dict()["qs_events"] == s["qs_events"] and st2.as_dict()["pairs"] == s["pairs"]

@@ -1,0 +1,73 @@
+"""Pins of the FP64 reference of the learned sampler (oracle/mlp.py): its
+backpropagation against central finite differences, the GELU identities, its
+bfloat16 rounding against torch's independent conversion, and Adam's first
+step against its closed form."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def _theta(seed=0, scale=0.3):
+    r = np.random.default_rng(seed)
+    return r.normal(0.0, scale, mlp.NPARAM)
+
+
+def test_backprop_matches_finite_differences():
+    r = np.random.default_rng(1)
+    theta = _theta(1)
+    X = r.uniform(-1, 1, (40, 2))
+    t = r.normal(size=40)
+    _, g = mlp.loss_and_grad(theta, X, t, round_bf16=False)
+    idx = np.concatenate([r.choice(mlp.NPARAM - 1, 60, replace=False), [mlp.NPARAM - 1, 0, 128, 192, 4288]])
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        lp, _ = mlp.loss_and_grad(tp, X, t, round_bf16=False)
+        lm, _ = mlp.loss_and_grad(tm, X, t, round_bf16=False)
+        fd = (lp - lm) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-9), i
+
+
+def test_gelu_identities_and_derivative():
+    x = np.linspace(-6, 6, 101)
+    assert np.allclose(mlp.gelu(x) - mlp.gelu(-x), x, atol=1e-14)  # tanh is odd
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert mlp.gelu(np.array([30.0]))[0] == pytest.approx(30.0)
+    h = 1e-6
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(x), fd, atol=1e-8)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(2)
+    v = np.concatenate([r.normal(0, 3, 5000), [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -1 - 2 ** -8, 0.0, 65504.0]])
+    ref = torch.tensor(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(v), ref)
+    assert mlp.bf16(np.array([1 + 2 ** -8]))[0] == 1.0          # tie to even
+    assert mlp.bf16(np.array([1 + 3 * 2 ** -8]))[0] == 1 + 2 ** -6
+
+
+def test_adam_first_step_is_signed_lr():
+    theta = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    new, m, v = mlp.adam(theta, np.zeros(3), np.zeros(3), g, 1, 0.01)
+    # bias-corrected first step: m/(sqrt(v)+eps) = g/|g| up to eps
+    assert np.allclose(new, theta - 0.01 * np.sign(g), atol=1e-7)
+
+
+def test_output_maps():
+    u = np.array([1e-6, 0.3, 0.7, 0.999])
+    y = np.array([0.2, -1.0, 0.4, 0.0])
+    qs = mlp.output(0, y, u)
+    assert np.all(qs <= 1.0) and np.allclose(np.log(qs[:3]), np.minimum(y[:3] + 3 * np.log(u[:3]), 0.0))
+    bw = mlp.output(1, np.array([0.2, 0.7, -0.1, 0.3]), u)
+    assert np.allclose(bw, [0.2, 0.5, 0.0, 0.3])
+    X = mlp.features(1, [1e-5, 1.0, 1e9], [0.2, 0.9, 0.5], 0.02, 1e3)
+    assert X[0, 0] == -1.0 and X[2, 0] == 1.0
+    assert np.allclose(X[:, 1], [2 * 0.4 - 1, 2 * 0.2 - 1, 1.0])
