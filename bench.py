@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--cascade-scale", type=float, default=0.1,
+                    help="fraction of the 64 patch counts round(10^(3+4U)) to run in the cascade leg")
+    ap.add_argument("--cascade-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -190,10 +195,11 @@ def counts(bufs):
     return sum(int(bufs[k].count.item()) for k in ("electrons", "positrons", "photons"))
 
 
-def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True):
+def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None):
     import torch
     stats = api.Stats()
-    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats)
+    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats,
+                           mlp=mlp)
     for s in range(warmup):
         call(step0 + s)
     torch.cuda.synchronize()
@@ -219,6 +225,55 @@ def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=T
     ev_ms = [a.elapsed_time(b) for a, b in evs] if evolve_events else []
     n_after = counts(bufs)
     return dict(ms=ms, n_before=n_before, n_after=n_after, evolve_ms=ev_ms, stats=stats.as_dict())
+
+
+def mlp_leg(api, tabs, bufs, fire, args, ws):
+    """The substep with the learned sampler in place of the 2-D tables, and the
+    two samplers alone on 1e8 (chi, U) pairs."""
+    import math
+
+    import torch
+
+    from paper_2110_00256_gb300 import surrogate
+    fine = api.qed_tables_generate(api.table_params(qs_n_chi=512, qs_n_xi=1024, bw_n_chi=512, bw_n_xi=1024))
+    mlp = api.Mlp(fine, seed=3)
+    t0 = time.perf_counter()
+    train = {p: surrogate.train(mlp, fine, p, n_samples=4_000_000, epochs=8, batch=65536) for p in (0, 1)}
+    train_s = time.perf_counter() - t0
+    k = max(3, args.steps // 4)
+    r = time_substep(api, tabs, bufs, fire, k, 2, ws, step0=1000, mlp=mlp)
+    ms = max_over_ranks(ws, r["ms"])
+    out = {"value": sum_over_ranks(ws, r["n_before"] * k) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k,
+           "train_s": round(train_s, 2), "train_final_loss": {p: round(train[p]["final_loss"], 6) for p in train}}
+    n = 100_000_000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    for p, name in ((0, "qs"), (1, "bw")):
+        ax = tabs.params.qs if p == 0 else tabs.params.bw
+        lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
+        chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
+        u = torch.rand(n, generator=g, device="cuda", dtype=torch.float64).clamp_(1e-15, 1 - 1e-15)
+        o = torch.empty_like(chi)
+        for label, fn in (("mlp", lambda: mlp.sample(p, chi, u, o)),
+                          ("table_f32", lambda: api.qed_table_sample(tabs, p, api.QED_F32, chi, u, o))):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out[f"{name}_{label}_samples_per_s"] = 3 * n / (e0.elapsed_time(e1) * 1e-3)
+        del chi, u, o
+        ks = surrogate.compare(mlp, fine, p, n=2_000_000, prec=api.QED_F64)
+        out[f"{name}_ks_table256_f32_vs_fp64_table"] = round(
+            surrogate.compare_tables(tabs, api.QED_F32, fine, api.QED_F64, p, n=2_000_000), 6)
+        out[f"{name}_ks_mlp_vs_fp64_table"] = round(ks["overall"], 5)
+        out[f"{name}_ks_mlp_vs_fp64_table_worst_bin"] = round(max(ks["bins"]), 5)
+    out["params_bytes_bf16"] = 2 * 4417
+    out["table_bytes_fp32_256x256"] = 2 * 256 * 256 * 4
+    return out
 
 
 def e2e_leg(api, t, bufs, fire, steps, ws):
@@ -366,6 +421,9 @@ def gpu_main(args):
         torch.cuda.empty_cache()
         bufs, fire = make_species(api, workloads, api.QED_F32, n, extra, SEED, rank)
 
+    if not args.no_mlp:
+        result.setdefault("paths", {})["fp32_mlp"] = mlp_leg(api, tabs, bufs, fire, args, ws)
+
     if not args.no_e2e:
         k = min(args.steps, 5)
         ms, n_step, bi, bo = e2e_leg(api, tabs, bufs, fire, k, ws)
@@ -373,6 +431,20 @@ def gpu_main(args):
         result["e2e"] = {"value": sum_over_ranks(ws, n_step * k) / (ms * 1e-3), "unit": UNIT,
                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": k,
                          "ms_per_step": ms / k}
+
+    if not args.no_cascade:
+        del bufs, fire
+        torch.cuda.empty_cache()
+        from paper_2110_00256_gb300 import cascade
+        c = cascade.run(tabs, steps=args.cascade_steps, scale=args.cascade_scale)
+        result["cascade"] = {"value": c["value"], "unit": UNIT, "steps": c["steps"], "patches": c["patches"],
+                             "electrons_start": c["electrons"], "particles_end": c["n_end"],
+                             "ms": round(c["ms"], 3), "launches_per_step": c["launches_per_step"],
+                             "graph": "all steps in one CUDA graph, step counter on the device",
+                             "tuned_evolve": c["tuned"], "events": c["stats"],
+                             "workload": "64 patches, counts round(10^(3+4U)) x %g (seed 7), e- beam gamma 2000 +-5%% "
+                                         "vs a0=100 linear plane wave (0.8 um), dt = T_L/200, photons < 2 m_e c^2 "
+                                         "discarded" % args.cascade_scale}
 
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

@@ -221,6 +221,73 @@ qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        qed_precision prec, const qed_fire_list *fire, void *stream);
 
 /* ------------------------------------------------------------------------- */
+/* many patches per launch                                                    */
+/* ------------------------------------------------------------------------- */
+/* A patch: the three species of one region of the simulation, each with its
+ * firing list.  Patch sizes may differ by orders of magnitude. */
+typedef struct {
+    qed_species electrons, positrons, photons;
+    qed_fire_list fire[3]; /* electrons, positrons, photons */
+} qed_patch;
+
+#define QED_MAX_PATCHES 1024
+typedef struct qed_batch qed_batch; /* opaque, library-owned */
+
+/* Copy the descriptors of n_patches patches (pointers, capacities; host array,
+ * not kept) into library-owned device memory.  The particle buffers stay the
+ * caller's.  Synchronises `stream`. */
+qed_status qed_batch_create(const qed_patch *patches, int32_t n_patches, qed_precision prec,
+                            qed_batch **out, void *stream);
+qed_status qed_batch_destroy(qed_batch *b);
+
+/* qed_substep for every patch of `b` (§3, §5), in five launches whatever the
+ * number of patches: zero the firing counts; one persistent evolution launch
+ * over all 3 x n species segments (tiles of every segment form one index
+ * space, so uneven patches share the grid); one pair-production launch over
+ * all photon firing lists; one photon-emission launch over all lepton firing
+ * lists; one launch clamping the counts (and advancing opts->d_step).  Stream-
+ * ordered, allocates nothing, graph-capturable.  Results per patch are those
+ * of qed_substep on that patch. */
+qed_status qed_substep_batched(const qed_tables *t, const qed_batch *b, double dt, uint64_t seed,
+                               int64_t step, const qed_substep_opts *opts, void *stream);
+
+/* Launch-shape tuner: times the evolution kernel of `b` (dry runs that read
+ * everything and store nothing, so the particles are untouched) for 128, 256
+ * and 512 threads per CTA and every CTA count per SM the registers allow, and
+ * keeps the fastest in `b` (used by qed_substep_batched unless opts override
+ * it).  Outputs may be NULL.  Synchronises `stream`. */
+qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t *threads_out,
+                           int32_t *ctas_per_sm_out, float *ms_out, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* particle push in an analytic plane wave (drives the cascade workload)     */
+/* ------------------------------------------------------------------------- */
+/* Not from the paper, whose substep runs inside a PIC code: a minimal pusher
+ * so that the substep can be exercised over many steps.  Units c = m_e = 1;
+ * lengths in hbar/(m_e c).  Phase phi = omega (t - direction x) + phase0;
+ * E = e0 (0, cos phi, 0) (linear) or e0 (0, cos phi, sin phi) (circular);
+ * B = direction x-hat cross E. */
+typedef struct {
+    double e0;            /* amplitude, units of E_s (= a0 * omega for a0 the normalised amplitude) */
+    double omega;         /* angular frequency, units of m_e c^2 / hbar                            */
+    double phase0;
+    int32_t polarization; /* 0 linear, 1 circular                                                   */
+    int32_t direction;    /* +1 or -1: the wave travels along direction * x                         */
+} qed_plane_wave;
+
+/* One step of dt at time t for every particle of `sp` (positions required):
+ * the fields at (x, t) are written into the species' E and B arrays; leptons
+ * (charge -1 or +1) get a relativistic Boris push (J. P. Boris, 1970), photons
+ * (charge 0) fly straight at c; then x += v dt. */
+qed_status qed_push_plane_wave(const qed_species *sp, double charge, const qed_plane_wave *wave, double t,
+                               double dt, qed_precision prec, void *stream);
+/* The same for every species of a batch (electrons -1, positrons +1, photons
+ * 0; every species of the batch must have positions) in one launch, at time
+ * t0 + step * dt, the step read from d_step when it is not NULL. */
+qed_status qed_push_batched(const qed_batch *b, const qed_plane_wave *wave, double t0, double dt,
+                            int64_t step, const int64_t *d_step, void *stream);
+
+/* ------------------------------------------------------------------------- */
 /* learned sampler (stands in for the 2-D tables of §3.1, §3.2)              */
 /* ------------------------------------------------------------------------- */
 /* Two small networks, one per process, each 2 -> 64 -> 64 -> 1 with the tanh

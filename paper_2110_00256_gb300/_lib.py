@@ -51,6 +51,15 @@ class FireList(C.Structure):
                 ("capacity", C.c_int64)]
 
 
+class PlaneWave(C.Structure):
+    _fields_ = [("e0", C.c_double), ("omega", C.c_double), ("phase0", C.c_double), ("polarization", C.c_int32),
+                ("direction", C.c_int32)]
+
+
+class Patch(C.Structure):
+    _fields_ = [("electrons", Species), ("positrons", Species), ("photons", Species), ("fire", FireList * 3)]
+
+
 class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
                 ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
@@ -83,6 +92,12 @@ SIGNATURES = {
                          C.POINTER(SubstepOpts), _S, C.POINTER(FireList), _P]),
     "qed_substep_noalloc": (_S, [_P, C.POINTER(Species), C.POINTER(Species), C.POINTER(Species), _D, _U64,
                                  _I64, C.POINTER(SubstepOpts), _S, _P]),
+    "qed_batch_create": (_S, [C.POINTER(Patch), C.c_int32, _S, C.POINTER(_P), _P]),
+    "qed_batch_destroy": (_S, [_P]),
+    "qed_substep_batched": (_S, [_P, _P, _D, _U64, _I64, C.POINTER(SubstepOpts), _P]),
+    "qed_tune_evolve": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float), _P]),
+    "qed_push_plane_wave": (_S, [C.POINTER(Species), _D, C.POINTER(PlaneWave), _D, _D, _S, _P]),
+    "qed_push_batched": (_S, [_P, C.POINTER(PlaneWave), _D, _D, _I64, _P, _P]),
     "qed_mlp_create": (_S, [_P, _U64, C.POINTER(_P), _P]),
     "qed_mlp_destroy": (_S, [_P]),
     "qed_mlp_get_params": (_S, [_P, _S, _P]),
@@ -93,6 +108,7 @@ SIGNATURES = {
     "qed_table_sample": (_S, [_P, _S, _S, _P, _P, _I64, _P, _P]),
 }
 QED_MLP_PARAMS = 4417
+QED_MAX_PATCHES = 1024
 QED_NOALLOC_MAX_PARTICLES = 1 << 20
 
 _lock = threading.Lock()

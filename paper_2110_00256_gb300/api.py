@@ -21,6 +21,8 @@ __all__ = [
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
+    "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave",
+    "qed_push_batched",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -337,3 +339,78 @@ def substep_opts_mlp(mlp: Mlp, photon_threshold=0.0, stats: Stats | None = None)
     o.sampler = 1
     o.mlp = mlp.handle.value
     return o
+
+
+# ---------------------------------------------------------------------------------------
+# many patches per launch
+# ---------------------------------------------------------------------------------------
+class Batch:
+    """Owning wrapper of a qed_batch* over a list of patches (dicts with
+    "electrons", "positrons", "photons" SpeciesBuffers and "fire", three FireBuffers)."""
+
+    def __init__(self, patches: list, prec: int, stream=None):
+        arr = (_lib.Patch * len(patches))()
+        for i, p in enumerate(patches):
+            arr[i].electrons = p["electrons"].struct()
+            arr[i].positrons = p["positrons"].struct()
+            arr[i].photons = p["photons"].struct()
+            for k in range(3):
+                arr[i].fire[k] = p["fire"][k].struct()
+        out = C.c_void_p()
+        check(lib().qed_batch_create(arr, len(patches), prec, C.byref(out), _stream(stream)))
+        self.handle = out
+        self.patches = patches  # keeps the buffers alive
+        self.prec = prec
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().qed_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def qed_substep_batched(t: Tables, b: Batch, dt: float, seed: int, step: int, opts: SubstepOpts | None = None,
+                        stream=None):
+    check(lib().qed_substep_batched(t.handle, b.handle, float(dt), int(seed), int(step),
+                                    C.byref(opts) if opts is not None else None, _stream(stream)))
+
+
+def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:
+    th, ct, ms = C.c_int32(), C.c_int32(), C.c_float()
+    check(lib().qed_tune_evolve(t.handle, b.handle, C.byref(th), C.byref(ct), C.byref(ms), _stream(stream)))
+    return {"threads": th.value, "ctas_per_sm": ct.value, "ms": ms.value}
+
+
+def make_opts(photon_threshold=0.0, stats: Stats | None = None, mlp: "Mlp | None" = None,
+              d_step: torch.Tensor | None = None, evolve_threads: int = 0, evolve_ctas_per_sm: int = 0) -> SubstepOpts:
+    o = _opts(photon_threshold, stats)
+    if mlp is not None:
+        o.sampler = 1
+        o.mlp = mlp.handle.value
+    if d_step is not None:
+        o.d_step = d_step.data_ptr()
+    o.evolve_threads = int(evolve_threads)
+    o.evolve_ctas_per_sm = int(evolve_ctas_per_sm)
+    return o
+
+
+# ---------------------------------------------------------------------------------------
+# plane-wave push (drives the cascade workload)
+# ---------------------------------------------------------------------------------------
+def plane_wave(e0: float, omega: float, phase0: float = 0.0, circular: bool = False, direction: int = -1):
+    return _lib.PlaneWave(float(e0), float(omega), float(phase0), 1 if circular else 0, int(direction))
+
+
+def qed_push_plane_wave(sp: SpeciesBuffers, charge: float, wave, t: float, dt: float, stream=None):
+    s = sp.struct()
+    check(lib().qed_push_plane_wave(C.byref(s), float(charge), C.byref(wave), float(t), float(dt), sp.prec,
+                                    _stream(stream)))
+
+
+def qed_push_batched(b: Batch, wave, t0: float, dt: float, step: int = 0, d_step: torch.Tensor | None = None,
+                     stream=None):
+    check(lib().qed_push_batched(b.handle, C.byref(wave), float(t0), float(dt), int(step),
+                                 d_step.data_ptr() if d_step is not None else None, _stream(stream)))

@@ -1,0 +1,391 @@
+// batched.cu -- the substep over many patches (each with its own electrons,
+// positrons and photons of uneven size) in five launches per step, whatever
+// the number of patches: zero the firing counts, one evolution launch over all
+// 3 x n segments, one pair-production launch over all photon firing lists, one
+// photon-emission launch over all lepton firing lists, one clamp.  The segment
+// descriptors live in device memory owned by a qed_batch (made once), so the
+// step allocates nothing and can be captured in a CUDA graph; with
+// opts->d_step a captured step replays as many steps.  qed_tune_evolve picks
+// the evolution launch shape (threads per CTA, CTAs per SM) by timing dry runs.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "events.cuh"
+#include "evolve.cuh"
+#include "pusher.cuh"
+
+namespace qed {
+
+qed_status check_opts(const qed_substep_opts *o);
+template <typename T>
+EventCommon<T> event_common(const qed_tables *t, int proc, uint64_t seed, int64_t step, const qed_substep_opts *o);
+
+struct ClampEntry {
+    unsigned long long *count;
+    int64_t cap;
+};
+
+}  // namespace qed
+
+struct qed_batch {
+    int device;
+    qed_precision prec;
+    int n_patches;
+    void *d_evolve;    // EvolveSeg<T>[3 n]: electrons, positrons, photons of patch 0, 1, ...
+    void *d_qs;        // EventSeg<T>[2 n]: electrons -> photons, positrons -> photons
+    void *d_bw;        // EventSeg<T>[n]: photons -> electrons, positrons
+    int64_t **d_zero;  // [3 n] firing counts to zero
+    qed::ClampEntry *d_clamp;  // [6 n] species and firing counts to clamp
+    void *d_push;      // PushSeg<T>[3 n] when every species has positions, else NULL
+    bool vec;
+    int64_t capacity_sum, fire_capacity_max;
+    int threads, ctas_per_sm;  // tuned evolution launch shape (0: default)
+};
+
+namespace qed {
+
+__global__ void zero_counts_kernel(int64_t *const *p, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *p[i] = 0;
+}
+
+__global__ void clamp_batch_kernel(const ClampEntry *e, int n, int64_t *step)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long *c = e[i].count;
+        if (*c > (unsigned long long)e[i].cap) *c = e[i].cap;
+    }
+    if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
+}
+
+// Block-wide prefix of the 32-entry chunk counts of n_seg firing lists into
+// s_end (inclusive); s_n receives the clamped list lengths.
+template <typename T>
+__device__ void chunk_prefix(const EventSeg<T> *segs, int n_seg, long long *s_end, long long *s_n, long long *s_warp)
+{
+    const int per = (n_seg + blockDim.x - 1) / blockDim.x;
+    const int s0 = threadIdx.x * per, s1 = min(n_seg, s0 + per);
+    long long local = 0;
+    for (int s = s0; s < s1; ++s) {
+        const long long n = fire_n(segs[s].fire_count, segs[s].fire_cap);
+        s_n[s] = n;
+        local += (n + 31) / 32;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    long long acc = incl - local;
+    for (int w = 0; w < warp; ++w) acc += s_warp[w];
+    for (int s = s0; s < s1; ++s) {
+        acc += (s_n[s] + 31) / 32;
+        s_end[s] = acc;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_seg(const long long *s_end, int n_seg, long long c)
+{
+    int lo = 0, hi = n_seg - 1;  // first s with s_end[s] > c
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_end[mid] > c)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// dynamic shared memory: [InferSmem if MLP][s_end n][s_n n]
+template <typename T, bool MLP, bool QS>
+__global__ void __launch_bounds__(256) event_batched_kernel(const EventSeg<T> *__restrict__ segs, int n_seg,
+                                                            const __grid_constant__ EventCommon<T> c)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_warp[8];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
+    long long *s_end = reinterpret_cast<long long *>(smem_raw + (MLP ? sizeof(InferSmem) : 0));
+    long long *s_n = s_end + n_seg;
+    if constexpr (MLP) mlp_stage(S.net, c.mlpv.w);
+    chunk_prefix<T>(segs, n_seg, s_end, s_n, s_warp);
+    const long long total = s_end[n_seg - 1];
+    const int64_t step = event_step(c.d_step, c.step);
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    EventCounts k;
+    for (long long ch = warp; ch < total; ch += nwarp) {
+        const int s = find_seg(s_end, n_seg, ch);
+        const int64_t base = (ch - (s ? s_end[s - 1] : 0)) * 32;
+        if constexpr (QS)
+            qs_event_chunk<T, MLP>(segs[s], c, step, base, s_n[s], S, k);
+        else
+            bw_event_chunk<T, MLP>(segs[s], c, step, base, s_n[s], S, k);
+    }
+    flush_counts(c.stats, k, QS);
+}
+
+template <typename T, bool QS>
+static qed_status launch_events_batched(const qed_batch *b, const EventCommon<T> &c, bool mlp, cudaStream_t st)
+{
+    const int n_seg = QS ? 2 * b->n_patches : b->n_patches;
+    const EventSeg<T> *segs = (const EventSeg<T> *)(QS ? b->d_qs : b->d_bw);
+    const size_t dyn = (mlp ? sizeof(InferSmem) : 0) + (size_t)n_seg * 2 * sizeof(long long);
+    int64_t warps = (b->fire_capacity_max * (QS ? 2 : 1) + 31) / 32;
+    int64_t grid = (warps + 7) / 8;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
+    // the opt-in shared-memory size is set once, for the largest batch
+    constexpr int kMaxDyn = (int)sizeof(InferSmem) + 2 * QED_MAX_PATCHES * 2 * (int)sizeof(long long);
+    if (mlp) {
+        auto k = event_batched_kernel<T, true, QS>;
+        static bool attr = false;
+        if (!attr) {
+            QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            attr = true;
+        }
+        k<<<(int)grid, 256, dyn, st>>>(segs, n_seg, c);
+    } else {
+        auto k = event_batched_kernel<T, false, QS>;
+        static bool attr = false;
+        if (!attr) {
+            QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            attr = true;
+        }
+        k<<<(int)grid, 256, dyn, st>>>(segs, n_seg, c);
+    }
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+template <typename T>
+static qed_status build_batch(const qed_patch *patches, int n, qed_batch *b, cudaStream_t st)
+{
+    std::vector<EvolveSeg<T>> ev(3 * (size_t)n);
+    std::vector<EventSeg<T>> qs(2 * (size_t)n), bw((size_t)n);
+    std::vector<int64_t *> zero(3 * (size_t)n);
+    std::vector<ClampEntry> clamp(6 * (size_t)n);
+    bool vec = true;
+    int64_t capsum = 0, fmax = 0;
+    for (int i = 0; i < n; ++i) {
+        const qed_patch &p = patches[i];
+        const qed_species *sp[3] = {&p.electrons, &p.positrons, &p.photons};
+        const int proc[3] = {QED_PROC_QS, QED_PROC_QS, QED_PROC_BW};
+        for (int k = 0; k < 3; ++k) {
+            vec = fill_seg<T>(ev[3 * i + k], sp[k], proc[k], &p.fire[k]) && vec;
+            zero[3 * i + k] = p.fire[k].d_count;
+            clamp[6 * i + k] = ClampEntry{(unsigned long long *)sp[k]->d_count, sp[k]->capacity};
+            clamp[6 * i + 3 + k] = ClampEntry{(unsigned long long *)p.fire[k].d_count, p.fire[k].capacity};
+            capsum += sp[k]->capacity;
+            fmax = fmax > p.fire[k].capacity ? fmax : p.fire[k].capacity;
+        }
+        for (int k = 0; k < 2; ++k) {
+            EventSeg<T> &g = qs[2 * i + k];
+            memset(&g, 0, sizeof(g));
+            g.parent = ptrs<T>(sp[k]);
+            g.out0 = ptrs<T>(&p.photons);
+            g.fire_idx = p.fire[k].idx, g.fire_chi = p.fire[k].chi, g.fire_count = p.fire[k].d_count;
+            g.fire_cap = p.fire[k].capacity;
+        }
+        EventSeg<T> &g = bw[i];
+        memset(&g, 0, sizeof(g));
+        g.parent = ptrs<T>(&p.photons);
+        g.out0 = ptrs<T>(&p.electrons);
+        g.out1 = ptrs<T>(&p.positrons);
+        g.fire_idx = p.fire[2].idx, g.fire_chi = p.fire[2].chi, g.fire_count = p.fire[2].d_count;
+        g.fire_cap = p.fire[2].capacity;
+    }
+    bool positions = true;
+    std::vector<PushSeg<T>> push(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const qed_species *sp[3] = {&patches[i].electrons, &patches[i].positrons, &patches[i].photons};
+        const double q[3] = {-1.0, 1.0, 0.0};
+        for (int k = 0; k < 3; ++k) {
+            positions = positions && sp[k]->x && sp[k]->y && sp[k]->z;
+            push[3 * i + k] = push_seg<T>(sp[k], q[k]);
+        }
+    }
+    if (positions) {
+        QED_CUDA_TRY(cudaMalloc(&b->d_push, push.size() * sizeof(PushSeg<T>)));
+        QED_CUDA_TRY(cudaMemcpyAsync(b->d_push, push.data(), push.size() * sizeof(PushSeg<T>), cudaMemcpyHostToDevice,
+                                     st));
+    }
+    struct Up {
+        void **dst;
+        const void *src;
+        size_t bytes;
+    } ups[5] = {{&b->d_evolve, ev.data(), ev.size() * sizeof(EvolveSeg<T>)},
+                {&b->d_qs, qs.data(), qs.size() * sizeof(EventSeg<T>)},
+                {&b->d_bw, bw.data(), bw.size() * sizeof(EventSeg<T>)},
+                {(void **)&b->d_zero, zero.data(), zero.size() * sizeof(int64_t *)},
+                {(void **)&b->d_clamp, clamp.data(), clamp.size() * sizeof(ClampEntry)}};
+    for (const Up &u : ups) {
+        QED_CUDA_TRY(cudaMalloc(u.dst, u.bytes));
+        QED_CUDA_TRY(cudaMemcpyAsync(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st));
+    }
+    QED_CUDA_TRY(cudaStreamSynchronize(st));
+    b->vec = vec;
+    b->capacity_sum = capsum;
+    b->fire_capacity_max = fmax;
+    return QED_OK;
+}
+
+template <typename T>
+static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, double dt, uint64_t seed, int64_t step,
+                                       const qed_substep_opts *o, cudaStream_t st)
+{
+    const int n = b->n_patches;
+    zero_counts_kernel<<<(3 * n + 255) / 256, 256, 0, st>>>(b->d_zero, 3 * n);
+    QED_LAUNCH_CHECK();
+    const int threads = (o && o->evolve_threads) ? o->evolve_threads : (b->threads ? b->threads : 256);
+    const int ctas = (o && o->evolve_ctas_per_sm) ? o->evolve_ctas_per_sm : b->ctas_per_sm;
+    if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
+    qed_status s = launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
+                                             o ? (long long *)o->d_stats : nullptr, 0, b->vec, threads, ctas, st);
+    if (s) return s;
+    if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
+    const bool mlp = o && o->sampler == 1;
+    if ((s = launch_events_batched<T, false>(b, event_common<T>(t, QED_PROC_BW, seed, step, o), mlp, st))) return s;
+    if ((s = launch_events_batched<T, true>(b, event_common<T>(t, QED_PROC_QS, seed, step, o), mlp, st))) return s;
+    clamp_batch_kernel<<<(6 * n + 255) / 256, 256, 0, st>>>(b->d_clamp, 6 * n, o ? o->d_step : nullptr);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+static void free_batch(qed_batch *b)
+{
+    if (!b) return;
+    void *p[] = {b->d_evolve, b->d_qs, b->d_bw, b->d_zero, b->d_clamp, b->d_push};
+    for (void *x : p)
+        if (x) cudaFree(x);
+    delete b;
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" qed_status qed_batch_create(const qed_patch *patches, int32_t n_patches, qed_precision prec,
+                                       qed_batch **out, void *stream)
+{
+    clear_error();
+    if (!out) QED_FAIL(QED_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!patches || n_patches <= 0 || n_patches > QED_MAX_PATCHES)
+        QED_FAIL(QED_ERR_INVALID_ARG, "need 1 <= n_patches <= %d (got %d)", QED_MAX_PATCHES, (int)n_patches);
+    qed_status s;
+    for (int i = 0; i < n_patches; ++i) {
+        if ((s = check_species(&patches[i].electrons, "electrons", prec))) return s;
+        if ((s = check_species(&patches[i].positrons, "positrons", prec))) return s;
+        if ((s = check_species(&patches[i].photons, "photons", prec))) return s;
+        for (int k = 0; k < 3; ++k)
+            if ((s = check_fire(&patches[i].fire[k], "fire"))) return s;
+    }
+    qed_batch *b = new qed_batch();
+    memset(b, 0, sizeof(*b));
+    cudaGetDevice(&b->device);
+    b->prec = prec;
+    b->n_patches = n_patches;
+    cudaStream_t st = as_stream(stream);
+    s = prec == QED_F32 ? build_batch<float>(patches, n_patches, b, st) : build_batch<double>(patches, n_patches, b, st);
+    if (s) {
+        free_batch(b);
+        return s;
+    }
+    *out = b;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_batch_destroy(qed_batch *b)
+{
+    clear_error();
+    free_batch(b);
+    return QED_OK;
+}
+
+extern "C" qed_status qed_substep_batched(const qed_tables *t, const qed_batch *b, double dt, uint64_t seed,
+                                          int64_t step, const qed_substep_opts *opts, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_tables(t))) return s;
+    if (!b) QED_FAIL(QED_ERR_INVALID_ARG, "batch is NULL");
+    if ((s = check_opts(opts))) return s;
+    if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    if (opts && opts->evolve_threads && opts->evolve_threads != 128 && opts->evolve_threads != 256 &&
+        opts->evolve_threads != 512)
+        QED_FAIL(QED_ERR_INVALID_ARG, "evolve_threads must be 128, 256 or 512");
+    if (opts && (opts->evolve_ctas_per_sm < 0 || opts->evolve_ctas_per_sm > 8))
+        QED_FAIL(QED_ERR_INVALID_ARG, "evolve_ctas_per_sm must be in [0, 8]");
+    cudaStream_t st = as_stream(stream);
+    return b->prec == QED_F32 ? substep_batched_impl<float>(t, b, dt, seed, step, opts, st)
+                              : substep_batched_impl<double>(t, b, dt, seed, step, opts, st);
+}
+
+extern "C" qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t *threads_out,
+                                      int32_t *ctas_per_sm_out, float *ms_out, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_tables(t))) return s;
+    if (!b) QED_FAIL(QED_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    QED_CUDA_TRY(cudaEventCreate(&e0));
+    QED_CUDA_TRY(cudaEventCreate(&e1));
+    const int cand_threads[3] = {128, 256, 512};
+    float best = 1e30f;
+    int bt = 256, bc = 0;
+    for (int th : cand_threads) {
+        const int max_ctas = 768 / th;  // the register budget of the kernel's launch bounds
+        for (int c = 1; c <= max_ctas && s == QED_OK; ++c) {
+            float tot = 0.f;
+            for (int rep = 0; rep < 4 && s == QED_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                s = b->prec == QED_F32
+                        ? launch_evolve_segments<float>((const EvolveSeg<float> *)b->d_evolve, 3 * b->n_patches,
+                                                        make_view<float>(t), 0.f, nullptr, 1, b->vec, th, c, st)
+                        : launch_evolve_segments<double>((const EvolveSeg<double> *)b->d_evolve, 3 * b->n_patches,
+                                                         make_view<double>(t), 0.0, nullptr, 1, b->vec, th, c, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;  // the first run warms up
+            }
+            if (s == QED_OK && tot / 3 < best) best = tot / 3, bt = th, bc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    b->threads = bt;
+    b->ctas_per_sm = bc;
+    if (threads_out) *threads_out = bt;
+    if (ctas_per_sm_out) *ctas_per_sm_out = bc;
+    if (ms_out) *ms_out = best;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_push_batched(const qed_batch *b, const qed_plane_wave *wave, double t0, double dt,
+                                       int64_t step, const int64_t *d_step, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if (!b) QED_FAIL(QED_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->d_push) QED_FAIL(QED_ERR_INVALID_ARG, "the batch's species have no positions");
+    if ((s = check_wave(wave))) return s;
+    if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    cudaStream_t st = as_stream(stream);
+    return b->prec == QED_F32
+               ? launch_push<float>(b->d_push, 3 * b->n_patches, wave_params(wave), t0, dt, d_step, step,
+                                    b->capacity_sum, st)
+               : launch_push<double>(b->d_push, 3 * b->n_patches, wave_params(wave), t0, dt, d_step, step,
+                                     b->capacity_sum, st);
+}

@@ -298,16 +298,24 @@ static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const Tab
 {
     const size_t dyn = (size_t)n_seg * 2 * sizeof(long long);
     int grid = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 768 / THREADS);
+    // the opt-in shared-memory size is set once per kernel, for the largest batch
+    constexpr int kMaxDyn = 3 * QED_MAX_PATCHES * 2 * (int)sizeof(long long);
     if (vec) {
         constexpr int V = sizeof(T) == 4 ? 4 : 2;
-        if (dyn > 48 * 1024)
+        static bool attr = false;
+        if (!attr) {
             QED_CUDA_TRY(cudaFuncSetAttribute(evolve_seg_kernel<T, V, THREADS>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            attr = true;
+        }
         evolve_seg_kernel<T, V, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
     } else {
-        if (dyn > 48 * 1024)
+        static bool attr = false;
+        if (!attr) {
             QED_CUDA_TRY(cudaFuncSetAttribute(evolve_seg_kernel<T, 1, THREADS>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            attr = true;
+        }
         evolve_seg_kernel<T, 1, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
     }
     QED_LAUNCH_CHECK();

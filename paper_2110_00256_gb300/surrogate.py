@@ -87,3 +87,19 @@ def compare(mlp: api.Mlp, tables: api.Tables, proc: int, n: int = 1_000_000, see
         m = (t >= edges[i].item()) & (t < edges[i + 1].item())
         out["bins"].append(ks_distance(key(xm[m]), key(xt[m])))
     return out
+
+
+def compare_tables(ta: api.Tables, prec_a: int, tb: api.Tables, prec_b: int, proc: int, n: int = 1_000_000,
+                   seed: int = 98) -> float:
+    """KS distance between the samples of two table sets on the same (chi, U)."""
+    p = tb.params
+    ax = p.qs if proc == api.QED_PROC_QS else p.bw
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
+    chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
+    u = torch.rand(n, generator=g, device="cuda", dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
+    a = api.qed_table_sample(ta, proc, prec_a, chi, u)
+    b = api.qed_table_sample(tb, proc, prec_b, chi, u)
+    key = (lambda v: torch.log(v)) if proc == api.QED_PROC_QS else (lambda v: v)
+    return ks_distance(key(a), key(b))
