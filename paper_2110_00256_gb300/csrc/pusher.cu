@@ -16,18 +16,23 @@ namespace qed {
 
 int sm_count();
 
-// phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E
+__device__ __forceinline__ void d_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void d_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+
+// phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E.
+// Evaluated in the working precision (over the cascade's 10 periods the FP32
+// phase keeps ~1e-5 rad).
 template <typename T>
 __device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, T &ex, T &ey, T &ez, T &bx, T &by,
                                             T &bz)
 {
-    const double phi = w.omega * (t - (double)w.direction * (double)x) + w.phase0;
-    double s, c;
-    sincos(phi, &s, &c);
-    ex = T(0);
-    ey = (T)(w.e0 * c);
-    ez = w.circular ? (T)(w.e0 * s) : T(0);
     const T d = (T)w.direction;
+    const T phi = (T)w.omega * ((T)t - d * x) + (T)w.phase0;
+    T s, c;
+    d_sincos(phi, &s, &c);
+    ex = T(0);
+    ey = (T)w.e0 * c;
+    ez = w.circular ? (T)w.e0 * s : T(0);
     bx = T(0);
     by = -d * ez;
     bz = d * ey;
