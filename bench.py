@@ -73,7 +73,7 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "physics.cuh", "common.cuh")
+KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "physics.cuh", "common.cuh", "pipeline.cuh")
 
 
 def kernel_hash() -> str:
@@ -195,11 +195,11 @@ def counts(bufs):
     return sum(int(bufs[k].count.item()) for k in ("electrons", "positrons", "photons"))
 
 
-def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None):
+def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None, shape=(0, 0, 0)):
     import torch
     stats = api.Stats()
     call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats,
-                           mlp=mlp)
+                           mlp=mlp, pipeline=shape[0], threads=shape[1], ctas_per_sm=shape[2])
     for s in range(warmup):
         call(step0 + s)
     torch.cuda.synchronize()
@@ -401,6 +401,17 @@ def gpu_main(args):
               "events_per_step": {k: v / (args.warmup + args.steps) for k, v in r["stats"].items() if v}}
     if clk:
         result["clocks"] = clk
+
+    # the evolution kernel's variants on the same workload (include/qed.h, QED_EVOLVE_*)
+    variants = {}
+    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0)), ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0)),
+                        ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0)),
+                        ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2))):
+        rv = time_substep(api, tabs, bufs, fire, 6, 2, ws, step0=500, shape=shape)
+        evm = sum(rv["evolve_ms"]) / len(rv["evolve_ms"])
+        variants[name] = {"evolve_ms": round(evm, 4), "hbm_gbs": round(BYTES_F32 * rv["n_before"] / (evm * 1e-3) / 1e9, 1),
+                          "wait_timeout": rv["stats"].get("wait_timeout", 0)}
+    result["evolve_variants"] = variants
 
     # FP64 table path beside it (same workload, FP64 SoA)
     if not args.no_fp64:

@@ -106,7 +106,10 @@ enum {
     QED_STAT_DROPPED_CAPACITY = 6,   /* events not executed: a destination was full       */
     QED_STAT_NONFINITE = 7,          /* particles with non-finite chi or optical depth    */
     QED_STAT_FIRE_OVERFLOW = 8,      /* firing particles beyond the fire-list capacity    */
-    QED_STAT_COUNT = 9
+    QED_STAT_WAIT_TIMEOUT = 9,       /* CTAs that gave up a bounded wait of the copy
+                                        pipeline (never expected; the launch's results
+                                        are then incomplete)                             */
+    QED_STAT_COUNT = 10
 };
 
 typedef struct {
@@ -124,7 +127,19 @@ typedef struct {
                                 at the end, so that one captured graph replays many steps   */
     int32_t evolve_threads;  /* evolution launch shape: threads per CTA (128, 256 or 512) and */
     int32_t evolve_ctas_per_sm; /* CTAs per SM (1..8); 0 = the library's default / tuned   */
+    int32_t evolve_pipeline; /* qed_substep's evolution kernel: QED_EVOLVE_DEFAULT, _DIRECT or
+                                _BULK (see below)                                            */
 } qed_substep_opts;
+
+/* How qed_substep's evolution reads the particle arrays.  DIRECT: every thread
+ * loads its particles with 16-byte loads into registers.  BULK (FP32, arrays
+ * 16-byte aligned; otherwise DIRECT): a producer warp per CTA copies whole
+ * tiles of every array into shared-memory stages with the bulk-copy engine,
+ * consumer warps evaluate them; evolve_threads 512 (16 consumer warps, 2
+ * stages) or evolve_ctas_per_sm 2 (8 warps, 2 stages) pick other shapes than
+ * the default (8 consumer warps, 4 stages, 1 CTA per SM).  Both give identical
+ * results.  DEFAULT is the faster of the two on GB300. */
+enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 
 /* ------------------------------------------------------------------------- */
 /* library                                                                   */

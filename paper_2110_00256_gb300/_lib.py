@@ -18,10 +18,11 @@ STATUS_NAMES = {0: "QED_OK", 1: "QED_ERR_INVALID_ARG", 2: "QED_ERR_CUDA", 3: "QE
                 4: "QED_ERR_NUMERIC", 5: "QED_ERR_TIMEOUT", 6: "QED_ERR_IO", 7: "QED_ERR_UNSUPPORTED"}
 QED_F32, QED_F64 = 0, 1
 QED_PROC_QS, QED_PROC_BW = 0, 1
+QED_EVOLVE_DEFAULT, QED_EVOLVE_DIRECT, QED_EVOLVE_BULK = 0, 1, 2
 QED_MAX_TABLE_N = 1024
 (QED_STAT_QS_EVENTS, QED_STAT_BW_EVENTS, QED_STAT_PHOTONS_KEPT, QED_STAT_PHOTONS_DISCARDED,
  QED_STAT_PAIRS, QED_STAT_BW_NO_PAIR, QED_STAT_DROPPED_CAPACITY, QED_STAT_NONFINITE,
- QED_STAT_FIRE_OVERFLOW, QED_STAT_COUNT) = range(10)
+ QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_COUNT) = range(11)
 
 
 class QedError(RuntimeError):
@@ -63,7 +64,8 @@ class Patch(C.Structure):
 class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
                 ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
-                ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32)]
+                ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32),
+                ("evolve_pipeline", C.c_int32)]
 
 
 _P = C.c_void_p

@@ -12,11 +12,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (QED_F32, QED_F64, QED_PROC_BW, QED_PROC_QS, QED_STAT_COUNT, FireList, QedError,
-                   SubstepOpts, TableAxis, TableParams, check, lib)
+from ._lib import (QED_EVOLVE_BULK, QED_EVOLVE_DEFAULT, QED_EVOLVE_DIRECT, QED_F32, QED_F64, QED_PROC_BW,
+                   QED_PROC_QS, QED_STAT_COUNT, FireList, QedError, SubstepOpts, TableAxis, TableParams, check,
+                   lib)
 
 __all__ = [
-    "QED_F32", "QED_F64", "QED_PROC_QS", "QED_PROC_BW", "QedError", "table_params", "Tables",
+    "QED_F32", "QED_F64", "QED_PROC_QS", "QED_PROC_BW", "QED_EVOLVE_DEFAULT", "QED_EVOLVE_DIRECT",
+    "QED_EVOLVE_BULK", "QedError", "table_params", "Tables",
     "SpeciesBuffers", "FireBuffers", "Stats", "qed_tables_generate", "qed_tables_create",
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
@@ -187,7 +189,7 @@ class Stats:
     """Device counters (QED_STAT_*)."""
 
     NAMES = ("qs_events", "bw_events", "photons_kept", "photons_discarded", "pairs", "bw_no_pair",
-             "dropped_capacity", "nonfinite", "fire_overflow")
+             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout")
 
     def __init__(self, device="cuda"):
         self.t = torch.zeros(QED_STAT_COUNT, dtype=torch.int64, device=device)
@@ -234,7 +236,8 @@ class SubstepCall:
 
     def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                  photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
-                 stats: Stats | None = None, mlp: "Mlp | None" = None):
+                 stats: Stats | None = None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0,
+                 ctas_per_sm: int = 0):
         self.t = t
         self.keep = (electrons, positrons, photons, fire, stats, mlp)
         self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
@@ -243,6 +246,9 @@ class SubstepCall:
         if mlp is not None:
             self.opts.sampler = 1
             self.opts.mlp = mlp.handle.value
+        self.opts.evolve_pipeline = int(pipeline)
+        self.opts.evolve_threads = int(threads)
+        self.opts.evolve_ctas_per_sm = int(ctas_per_sm)
         self.dt = float(dt)
         self.seed = int(seed)
         self.prec = electrons.prec
@@ -255,8 +261,11 @@ class SubstepCall:
 
 def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
-                stream=None, mlp: "Mlp | None" = None):
-    SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp)(step, stream)
+                stream=None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0, ctas_per_sm: int = 0):
+    """One substep (include/qed.h).  pipeline / threads / ctas_per_sm choose the
+    evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library default)."""
+    SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp, pipeline, threads,
+                ctas_per_sm)(step, stream)
 
 
 def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
@@ -385,7 +394,8 @@ def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:
 
 
 def make_opts(photon_threshold=0.0, stats: Stats | None = None, mlp: "Mlp | None" = None,
-              d_step: torch.Tensor | None = None, evolve_threads: int = 0, evolve_ctas_per_sm: int = 0) -> SubstepOpts:
+              d_step: torch.Tensor | None = None, evolve_threads: int = 0, evolve_ctas_per_sm: int = 0,
+              evolve_pipeline: int = 0) -> SubstepOpts:
     o = _opts(photon_threshold, stats)
     if mlp is not None:
         o.sampler = 1
@@ -394,6 +404,7 @@ def make_opts(photon_threshold=0.0, stats: Stats | None = None, mlp: "Mlp | None
         o.d_step = d_step.data_ptr()
     o.evolve_threads = int(evolve_threads)
     o.evolve_ctas_per_sm = int(evolve_ctas_per_sm)
+    o.evolve_pipeline = int(evolve_pipeline)
     return o
 
 

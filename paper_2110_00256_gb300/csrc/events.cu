@@ -183,6 +183,8 @@ qed_status check_opts(const qed_substep_opts *o)
     if (o && o->sampler != 0 && o->sampler != 1) QED_FAIL(QED_ERR_INVALID_ARG, "unknown sampler %d", o->sampler);
     if (o && o->sampler == 1 && o->mlp == nullptr) QED_FAIL(QED_ERR_INVALID_ARG, "sampler 1 needs opts->mlp");
     if (o && !(o->photon_threshold >= 0.0)) QED_FAIL(QED_ERR_INVALID_ARG, "photon_threshold must be >= 0");
+    if (o && (o->evolve_pipeline < QED_EVOLVE_DEFAULT || o->evolve_pipeline > QED_EVOLVE_BULK))
+        QED_FAIL(QED_ERR_INVALID_ARG, "unknown evolve_pipeline %d", o->evolve_pipeline);
     return QED_OK;
 }
 
@@ -203,7 +205,9 @@ static qed_status substep_impl(const qed_tables *t, const qed_species *e, const 
     zero3<<<1, 32, 0, st>>>(fire[0].d_count, fire[1].d_count, fire[2].d_count);
     QED_LAUNCH_CHECK();
     if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
-    qed_status s = launch_evolve<T, 4>(a, vec, e->capacity + p->capacity + g->capacity, 0, st);
+    qed_status s = launch_evolve<T, 4>(a, vec, e->capacity + p->capacity + g->capacity, 0, st,
+                                       o ? o->evolve_pipeline : 0, o ? o->evolve_threads : 0,
+                                       o ? o->evolve_ctas_per_sm : 0);
     if (s) return s;
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
     // the event kernels clamp the firing counts on read and the species counts

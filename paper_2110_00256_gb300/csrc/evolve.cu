@@ -13,6 +13,7 @@
 
 #include "evolve.cuh"
 #include "physics.cuh"
+#include "pipeline.cuh"
 
 namespace qed {
 
@@ -94,50 +95,18 @@ __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_b
     }
 }
 
-// One tile: THREADS x VEC consecutive particles of segment `sg` starting at
-// tile index `first`.  dry != 0 evaluates everything but stores nothing (used
-// by the launch-shape tuner).
-template <typename T, int VEC, int THREADS>
-__device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, long long first, const T *s_qs,
-                                            const T *s_bw, const TablesView<T> &tab, T dt, long long *stats,
-                                            int dry, int &bad)
+// Evaluate, store and compact VEC particles [i0, i0 + VEC) of segment `sg`
+// whose inputs are already in registers (full: all VEC are live).  dry != 0
+// evaluates everything but stores nothing (used by the launch-shape tuner).
+template <typename T, int VEC>
+__device__ __forceinline__ void evolve_regs(const EvolveSeg<T> &sg, int64_t n, int64_t i0, bool full,
+                                            const T (&px)[VEC], const T (&py)[VEC], const T (&pz)[VEC],
+                                            const T (&ex)[VEC], const T (&ey)[VEC], const T (&ez)[VEC],
+                                            const T (&bx)[VEC], const T (&by)[VEC], const T (&bz)[VEC], T (&tau)[VEC],
+                                            T (&tc)[VEC], const T *s_qs, const T *s_bw, const TablesView<T> &tab,
+                                            T dt, long long *stats, int dry, int &bad)
 {
     const unsigned lane = threadIdx.x & 31u;
-    const int64_t i0 = first * ((int64_t)THREADS * VEC) + (int64_t)threadIdx.x * VEC;
-
-    T px[VEC], py[VEC], pz[VEC], ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC], tau[VEC], tc[VEC];
-    const bool full = i0 + VEC <= n;
-    if (full) {
-        load_vec<T, VEC>(sg.px, i0, px);
-        load_vec<T, VEC>(sg.py, i0, py);
-        load_vec<T, VEC>(sg.pz, i0, pz);
-        load_vec<T, VEC>(sg.ex, i0, ex);
-        load_vec<T, VEC>(sg.ey, i0, ey);
-        load_vec<T, VEC>(sg.ez, i0, ez);
-        load_vec<T, VEC>(sg.bx, i0, bx);
-        load_vec<T, VEC>(sg.by, i0, by);
-        load_vec<T, VEC>(sg.bz, i0, bz);
-        load_vec<T, VEC>(sg.tau, i0, tau);
-        if constexpr (sizeof(T) == 4) load_vec<T, VEC>(sg.tau_c, i0, tc);
-    } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            const int64_t i = i0 + j;
-            const bool v = i < n;
-            px[j] = v ? sg.px[i] : T(0);
-            py[j] = v ? sg.py[i] : T(0);
-            pz[j] = v ? sg.pz[i] : T(0);
-            ex[j] = v ? sg.ex[i] : T(0);
-            ey[j] = v ? sg.ey[i] : T(0);
-            ez[j] = v ? sg.ez[i] : T(0);
-            bx[j] = v ? sg.bx[i] : T(0);
-            by[j] = v ? sg.by[i] : T(0);
-            bz[j] = v ? sg.bz[i] : T(0);
-            tau[j] = v ? sg.tau[i] : T(1);
-            if constexpr (sizeof(T) == 4) tc[j] = v ? sg.tau_c[i] : T(0);
-        }
-    }
-
     bool fire[VEC];
     T chi[VEC];
     int cnt = 0;
@@ -195,6 +164,59 @@ __device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, l
     }
 }
 
+// scalar loads of the live particles among [i0, i0 + VEC) (ragged tail, misaligned arrays)
+template <typename T, int VEC>
+__device__ __forceinline__ void load_scalar(const EvolveSeg<T> &sg, int64_t n, int64_t i0, T (&px)[VEC],
+                                            T (&py)[VEC], T (&pz)[VEC], T (&ex)[VEC], T (&ey)[VEC], T (&ez)[VEC],
+                                            T (&bx)[VEC], T (&by)[VEC], T (&bz)[VEC], T (&tau)[VEC], T (&tc)[VEC])
+{
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        const int64_t i = i0 + j;
+        const bool v = i < n;
+        px[j] = v ? sg.px[i] : T(0);
+        py[j] = v ? sg.py[i] : T(0);
+        pz[j] = v ? sg.pz[i] : T(0);
+        ex[j] = v ? sg.ex[i] : T(0);
+        ey[j] = v ? sg.ey[i] : T(0);
+        ez[j] = v ? sg.ez[i] : T(0);
+        bx[j] = v ? sg.bx[i] : T(0);
+        by[j] = v ? sg.by[i] : T(0);
+        bz[j] = v ? sg.bz[i] : T(0);
+        tau[j] = v ? sg.tau[i] : T(1);
+        tc[j] = (sizeof(T) == 4 && v) ? sg.tau_c[i] : T(0);
+    }
+}
+
+// One tile: THREADS x VEC consecutive particles of segment `sg` starting at
+// tile index `first`, loaded straight from global memory.
+template <typename T, int VEC, int THREADS>
+__device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, long long first, const T *s_qs,
+                                            const T *s_bw, const TablesView<T> &tab, T dt, long long *stats,
+                                            int dry, int &bad)
+{
+    const int64_t i0 = first * ((int64_t)THREADS * VEC) + (int64_t)threadIdx.x * VEC;
+    T px[VEC], py[VEC], pz[VEC], ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC], tau[VEC], tc[VEC];
+    const bool full = i0 + VEC <= n;
+    if (full) {
+        load_vec<T, VEC>(sg.px, i0, px);
+        load_vec<T, VEC>(sg.py, i0, py);
+        load_vec<T, VEC>(sg.pz, i0, pz);
+        load_vec<T, VEC>(sg.ex, i0, ex);
+        load_vec<T, VEC>(sg.ey, i0, ey);
+        load_vec<T, VEC>(sg.ez, i0, ez);
+        load_vec<T, VEC>(sg.bx, i0, bx);
+        load_vec<T, VEC>(sg.by, i0, by);
+        load_vec<T, VEC>(sg.bz, i0, bz);
+        load_vec<T, VEC>(sg.tau, i0, tau);
+        if constexpr (sizeof(T) == 4) load_vec<T, VEC>(sg.tau_c, i0, tc);
+    } else {
+        load_scalar<T, VEC>(sg, n, i0, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc);
+    }
+    evolve_regs<T, VEC>(sg, n, i0, full, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt, stats,
+                        dry, bad);
+}
+
 // segments as kernel parameters (a few species)
 template <typename T, int VEC, int MAXSEG>
 __global__ void __launch_bounds__(kEvolveThreads, 3)
@@ -228,6 +250,201 @@ __global__ void __launch_bounds__(kEvolveThreads, 3)
                                             a.stats, 0, bad);
     }
     if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy pipeline (FP32, 16-byte-aligned arrays).  The last warp of the CTA
+// is the producer: for every full tile of TP = CW x 32 x 4 particles, eleven of
+// its lanes each issue one cp.async.bulk of that tile of one array (px .. bz,
+// tau, tau_c; TP x 4 bytes) into a shared-memory stage, counted on the stage's
+// `full` mbarrier.  The CW consumer warps read the stage with conflict-free
+// float4 loads (4 consecutive particles per thread), release it on the `empty`
+// mbarrier (one arrival per warp) before they compute, evaluate, and store the
+// optical depths with 16-byte streaming stores.  The ragged last tile of a
+// segment is not copied: its consumers load it from global memory.  S stages
+// keep S - 1 tiles of every SM's stream in flight while one is evaluated.
+// ---------------------------------------------------------------------------
+constexpr int kBulkArrays = 11;
+
+__device__ __forceinline__ const float *bulk_src(const EvolveSeg<float> &g, int k)
+{
+    switch (k) {
+    case 0: return g.px;
+    case 1: return g.py;
+    case 2: return g.pz;
+    case 3: return g.ex;
+    case 4: return g.ey;
+    case 5: return g.ez;
+    case 6: return g.bx;
+    case 7: return g.by;
+    case 8: return g.bz;
+    case 9: return g.tau;
+    default: return g.tau_c;
+    }
+}
+
+// bounded wait that also gives up as soon as another warp has given up
+__device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort || clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_give_up(int *abort, long long *stats)
+{
+    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+}
+
+template <int CW, int S>
+constexpr size_t kBulkStageBytes = (size_t)S * kBulkArrays * CW * 32 * 4 * sizeof(float);
+
+template <int CW, int S, int MINB, int MAXSEG>
+__global__ void __launch_bounds__((CW + 1) * 32, MINB)
+    evolve_bulk_kernel(const __grid_constant__ EvolveArgs<float, MAXSEG> a)
+{
+    constexpr int TP = CW * 32 * 4;
+    extern __shared__ __align__(128) float s_stage[];  // [S][kBulkArrays][TP]
+    __shared__ __align__(8) uint64_t s_full[S];
+    __shared__ __align__(8) uint64_t s_empty[S];
+    __shared__ float s_qs[QED_MAX_TABLE_N];
+    __shared__ float s_bw[QED_MAX_TABLE_N];
+    __shared__ long long s_end[MAXSEG];
+    __shared__ long long s_n[MAXSEG];
+    __shared__ int s_abort;
+
+    for (int i = threadIdx.x; i < a.tab.qs_G.n; i += blockDim.x) s_qs[i] = a.tab.qs_G.ln_f[i];
+    for (int i = threadIdx.x; i < a.tab.bw_T.n; i += blockDim.x) s_bw[i] = a.tab.bw_T.ln_f[i];
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int s = 0; s < a.n_seg; ++s) {
+            long long n = *a.seg[s].count;
+            n = n < 0 ? 0 : (n > a.seg[s].capacity ? a.seg[s].capacity : n);
+            s_n[s] = n;
+            acc += (n + TP - 1) / TP;
+            s_end[s] = acc;
+        }
+        s_abort = 0;
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&s_full[k], 1);
+            mbar_init(&s_empty[k], CW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const long long total = a.n_seg ? s_end[a.n_seg - 1] : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = &s_abort;
+
+    if (warp == CW) {  // producer
+        const uint64_t pol = l2_evict_first();
+        int k = 0;
+        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+            const int st = k % S;
+            const uint32_t ph = (uint32_t)(k / S) & 1u;
+            int s = 0;
+            while (t >= s_end[s]) ++s;
+            const int64_t i0 = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
+            const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_empty[st], ph ^ 1u, abort));
+            if (!ok) {
+                if (lane == 0) bulk_give_up(&s_abort, a.stats);
+                break;
+            }
+            if (i0 + TP <= s_n[s]) {
+                if (lane == 0) mbar_arrive_expect_tx(&s_full[st], kBulkArrays * TP * (uint32_t)sizeof(float));
+                __syncwarp();
+                if (lane < kBulkArrays)
+                    bulk_g2s(s_stage + ((size_t)st * kBulkArrays + lane) * TP, bulk_src(a.seg[s], lane) + i0,
+                             TP * (uint32_t)sizeof(float), &s_full[st], pol);
+            } else if (lane == 0) {
+                mbar_arrive(&s_full[st]);
+            }
+        }
+        // leave only once the copies of the last S tiles have landed
+        for (int j = 1; j <= S && j <= k; ++j) {
+            const int kk = k - j;
+            if (!mbar_wait(&s_full[kk % S], (uint32_t)(kk / S) & 1u) && lane == 0) bulk_give_up(&s_abort, a.stats);
+        }
+        return;
+    }
+
+    int bad = 0;
+    int k = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int st = k % S;
+        const uint32_t ph = (uint32_t)(k / S) & 1u;
+        int s = 0;
+        while (t >= s_end[s]) ++s;
+        const EvolveSeg<float> &sg = a.seg[s];
+        const int64_t n = s_n[s];
+        const int64_t base = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
+        const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+        const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_full[st], ph, abort));
+        if (!ok) {
+            if (lane == 0) bulk_give_up(&s_abort, a.stats);
+            break;
+        }
+        float px[4], py[4], pz[4], ex[4], ey[4], ez[4], bx[4], by[4], bz[4], tau[4], tc[4];
+        bool full4;
+        if (base + TP <= n) {
+            const float4 *v = reinterpret_cast<const float4 *>(s_stage + (size_t)st * kBulkArrays * TP) + threadIdx.x;
+            constexpr int q = TP / 4;
+            float4 w;
+#define QED_UNPACK(arr, k)                                 \
+    w = v[(k) * q];                                        \
+    arr[0] = w.x, arr[1] = w.y, arr[2] = w.z, arr[3] = w.w;
+            QED_UNPACK(px, 0) QED_UNPACK(py, 1) QED_UNPACK(pz, 2);
+            QED_UNPACK(ex, 3) QED_UNPACK(ey, 4) QED_UNPACK(ez, 5);
+            QED_UNPACK(bx, 6) QED_UNPACK(by, 7) QED_UNPACK(bz, 8);
+            QED_UNPACK(tau, 9) QED_UNPACK(tc, 10);
+#undef QED_UNPACK
+            full4 = true;
+        } else {
+            full4 = i0 + 4 <= n;
+            if (full4) {
+                load_vec<float, 4>(sg.px, i0, px);
+                load_vec<float, 4>(sg.py, i0, py);
+                load_vec<float, 4>(sg.pz, i0, pz);
+                load_vec<float, 4>(sg.ex, i0, ex);
+                load_vec<float, 4>(sg.ey, i0, ey);
+                load_vec<float, 4>(sg.ez, i0, ez);
+                load_vec<float, 4>(sg.bx, i0, bx);
+                load_vec<float, 4>(sg.by, i0, by);
+                load_vec<float, 4>(sg.bz, i0, bz);
+                load_vec<float, 4>(sg.tau, i0, tau);
+                load_vec<float, 4>(sg.tau_c, i0, tc);
+            } else {
+                load_scalar<float, 4>(sg, n, i0, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[st]);
+        evolve_regs<float, 4>(sg, n, i0, full4, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, a.tab,
+                              a.dt, a.stats, 0, bad);
+    }
+    if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
+}
+
+template <int CW, int S, int MINB, int MAXSEG>
+static qed_status launch_bulk(const EvolveArgs<float, MAXSEG> &a, int64_t capacity_sum, cudaStream_t st)
+{
+    constexpr size_t dyn = kBulkStageBytes<CW, S>;
+    static bool attr = false;
+    if (!attr) {
+        QED_CUDA_TRY(cudaFuncSetAttribute(evolve_bulk_kernel<CW, S, MINB, MAXSEG>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        attr = true;
+    }
+    constexpr int64_t tp = (int64_t)CW * 32 * 4;
+    const int64_t tiles = (capacity_sum + tp - 1) / tp;
+    int64_t g = (int64_t)sm_count() * MINB;
+    if (tiles < g) g = tiles < 1 ? 1 : tiles;
+    evolve_bulk_kernel<CW, S, MINB, MAXSEG><<<(int)g, (CW + 1) * 32, dyn, st>>>(a);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
 }
 
 // Segments in device memory (many patches): every CTA reads all segment
@@ -379,10 +596,17 @@ static int evolve_grid(int64_t total_particles)
 
 template <typename T, int MAXSEG>
 qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t capacity_sum, int grid_override,
-                         cudaStream_t st)
+                         cudaStream_t st, int pipeline, int threads, int ctas_per_sm)
 {
     // the grid is sized from the capacities (counts live on the device); idle
     // CTAs exit after reading the counts
+    if constexpr (sizeof(T) == 4) {
+        if (vec_ok && pipeline == QED_EVOLVE_BULK && grid_override <= 0) {
+            if (threads == 512) return launch_bulk<16, 2, 1, MAXSEG>(a, capacity_sum, st);
+            if (ctas_per_sm == 2) return launch_bulk<8, 2, 2, MAXSEG>(a, capacity_sum, st);
+            return launch_bulk<8, 4, 1, MAXSEG>(a, capacity_sum, st);
+        }
+    }
     if (vec_ok) {
         constexpr int V = sizeof(T) == 4 ? 4 : 2;
         const int g = grid_override > 0 ? grid_override : evolve_grid<T, V, MAXSEG>(capacity_sum);
@@ -395,12 +619,10 @@ qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t ca
     return QED_OK;
 }
 
-template qed_status launch_evolve<float, 4>(const EvolveArgs<float, 4> &, bool, int64_t, int, cudaStream_t);
-template qed_status launch_evolve<double, 4>(const EvolveArgs<double, 4> &, bool, int64_t, int, cudaStream_t);
-template qed_status launch_evolve<float, kMaxSegments>(const EvolveArgs<float, kMaxSegments> &, bool, int64_t, int,
-                                                       cudaStream_t);
-template qed_status launch_evolve<double, kMaxSegments>(const EvolveArgs<double, kMaxSegments> &, bool, int64_t, int,
-                                                        cudaStream_t);
+template qed_status launch_evolve<float, 4>(const EvolveArgs<float, 4> &, bool, int64_t, int, cudaStream_t, int, int,
+                                           int);
+template qed_status launch_evolve<double, 4>(const EvolveArgs<double, 4> &, bool, int64_t, int, cudaStream_t, int,
+                                            int, int);
 
 static bool al16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
 

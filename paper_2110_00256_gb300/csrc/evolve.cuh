@@ -12,10 +12,6 @@ constexpr int kEvolveThreads = 256;
 template <typename T, int VEC>
 constexpr int64_t kEvolveTile = (int64_t)kEvolveThreads * VEC;
 
-// segments per launch of the batched (patch) evolution; the descriptors travel
-// as kernel parameters (__grid_constant__), so no device memory is involved
-constexpr int kMaxSegments = 64;
-
 template <typename T>
 struct EvolveSeg {
     const T *px, *py, *pz, *ex, *ey, *ez, *bx, *by, *bz;
@@ -40,9 +36,11 @@ struct EvolveArgs {
 
 int sm_count();
 
+// pipeline: QED_EVOLVE_* (the bulk-copy pipeline applies to FP32 with
+// 16-byte-aligned arrays; threads 512 or ctas_per_sm 2 pick its other shapes)
 template <typename T, int MAXSEG>
 qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t capacity_sum, int grid_override,
-                         cudaStream_t st);
+                         cudaStream_t st, int pipeline = 0, int threads = 0, int ctas_per_sm = 0);
 
 template <typename T>
 bool fill_seg(EvolveSeg<T> &g, const qed_species *sp, int proc, const qed_fire_list *fire);

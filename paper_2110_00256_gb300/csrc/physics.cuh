@@ -26,40 +26,68 @@ constexpr double kTSmall = 0.22963966338592293;
 constexpr double kTLarge = 0.37961230854357125;
 
 // chi of a lepton, §2: chi^2 = (gamma E + p x B)^2 - (p.E)^2 in these units.
-// With n = p/|p| and E_perp = E - (n.E) n the same quantity is the sum of
+// FP32: with n = p/|p| and E_perp = E - (n.E) n the same quantity is the sum of
 // squares |gamma E_perp + p x B|^2 + (n.E)^2 (expand gamma^2 = 1 + p^2 and use
 // p x B perpendicular to n), which avoids the cancellation of the difference
-// form when chi is small against gamma |E| + |p| |B|.  A particle at rest has
-// chi = |E|.  Returns chi and gamma; NaN inputs give NaN.
-template <typename T>
-__device__ __forceinline__ T chi_lepton(T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T &gamma)
+// form when chi is small against gamma |E| + |p| |B|; a particle at rest has
+// chi = |E|.  FP64 keeps the difference form: its cancellation error, 1e-16
+// (S/chi)^2 relative, is below the FP64 tolerance, and it saves the FP64
+// square root and division of n, FP64 being GB300's scarce unit.
+// Returns chi and gamma; NaN inputs give NaN.
+__device__ __forceinline__ float chi_lepton(float px, float py, float pz, float ex, float ey, float ez, float bx,
+                                            float by, float bz, float &gamma)
 {
-    const T p2 = px * px + py * py + pz * pz;
-    gamma = d_sqrt(T(1) + p2);
-    const T pm = d_sqrt(p2);
-    const T inv = pm > T(0) ? T(1) / pm : T(0);
-    const T nx = px * inv, ny = py * inv, nz = pz * inv;
-    const T ne = nx * ex + ny * ey + nz * ez;
-    const T fx = gamma * (ex - ne * nx) + (py * bz - pz * by);
-    const T fy = gamma * (ey - ne * ny) + (pz * bx - px * bz);
-    const T fz = gamma * (ez - ne * nz) + (px * by - py * bx);
-    const T s = fx * fx + fy * fy + fz * fz + (pm > T(0) ? ne * ne : ex * ex + ey * ey + ez * ez);
-    return d_sqrt(s);
+    const float p2 = px * px + py * py + pz * pz;
+    gamma = sqrtf(1.0f + p2);
+    const float pm = sqrtf(p2);
+    const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
+    const float nx = px * inv, ny = py * inv, nz = pz * inv;
+    const float ne = nx * ex + ny * ey + nz * ez;
+    const float fx = gamma * (ex - ne * nx) + (py * bz - pz * by);
+    const float fy = gamma * (ey - ne * ny) + (pz * bx - px * bz);
+    const float fz = gamma * (ez - ne * nz) + (px * by - py * bx);
+    const float s = fx * fx + fy * fy + fz * fz + (pm > 0.0f ? ne * ne : ex * ex + ey * ey + ez * ez);
+    return sqrtf(s);
 }
 
-// chi_gamma of a photon, §2 (gamma -> |p|, v -> c n): chi_gamma = | |p| E_perp +
-// p x B |, the perpendicular part of |p| E + p x B.  Returns chi and |p|.
-template <typename T>
-__device__ __forceinline__ T chi_photon(T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T &pm)
+__device__ __forceinline__ double chi_lepton(double px, double py, double pz, double ex, double ey, double ez,
+                                             double bx, double by, double bz, double &gamma)
 {
-    pm = d_sqrt(px * px + py * py + pz * pz);
-    const T inv = pm > T(0) ? T(1) / pm : T(0);
-    const T nx = px * inv, ny = py * inv, nz = pz * inv;
-    const T ne = nx * ex + ny * ey + nz * ez;
-    const T fx = pm * (ex - ne * nx) + (py * bz - pz * by);
-    const T fy = pm * (ey - ne * ny) + (pz * bx - px * bz);
-    const T fz = pm * (ez - ne * nz) + (px * by - py * bx);
-    return d_sqrt(fx * fx + fy * fy + fz * fz);
+    gamma = sqrt(1.0 + (px * px + py * py + pz * pz));
+    const double fx = gamma * ex + (py * bz - pz * by);
+    const double fy = gamma * ey + (pz * bx - px * bz);
+    const double fz = gamma * ez + (px * by - py * bx);
+    const double pe = px * ex + py * ey + pz * ez;
+    const double s = fx * fx + fy * fy + fz * fz - pe * pe;
+    return sqrt(s < 0.0 ? 0.0 : s);  // (NaN stays NaN)
+}
+
+// chi_gamma of a photon, §2 (gamma -> |p|, v -> c n).  FP32: | |p| E_perp + p x B |,
+// the perpendicular part of |p| E + p x B; FP64: the difference form.  Returns
+// chi and |p|.
+__device__ __forceinline__ float chi_photon(float px, float py, float pz, float ex, float ey, float ez, float bx,
+                                            float by, float bz, float &pm)
+{
+    pm = sqrtf(px * px + py * py + pz * pz);
+    const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
+    const float nx = px * inv, ny = py * inv, nz = pz * inv;
+    const float ne = nx * ex + ny * ey + nz * ez;
+    const float fx = pm * (ex - ne * nx) + (py * bz - pz * by);
+    const float fy = pm * (ey - ne * ny) + (pz * bx - px * bz);
+    const float fz = pm * (ez - ne * nz) + (px * by - py * bx);
+    return sqrtf(fx * fx + fy * fy + fz * fz);
+}
+
+__device__ __forceinline__ double chi_photon(double px, double py, double pz, double ex, double ey, double ez,
+                                             double bx, double by, double bz, double &pm)
+{
+    pm = sqrt(px * px + py * py + pz * pz);
+    const double fx = pm * ex + (py * bz - pz * by);
+    const double fy = pm * ey + (pz * bx - px * bz);
+    const double fz = pm * ez + (px * by - py * bx);
+    const double pe = px * ex + py * ey + pz * ez;
+    const double s = fx * fx + fy * fy + fz * fz - pe * pe;
+    return sqrt(s < 0.0 ? 0.0 : s);
 }
 
 // log-log interpolation of a 1-D table held in `tab` (shared or global):

@@ -76,3 +76,31 @@ def test_kernel_asymptote_constants_match_closed_forms():
     gen = open(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "tablegen.cu")).read()
     c = float(re.search(r"\(([0-9.]+) /\* sqrt\(3\) / \(2 pi\) \*/\)", gen).group(1))
     assert c == pytest.approx(math.sqrt(3) / (2 * math.pi), rel=1e-15)
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """Every ctypes Structure of the binding has the size and field offsets
+    that a C compiler gives the matching struct of include/qed.h."""
+    import subprocess
+    from paper_2110_00256_gb300 import _lib
+    pairs = {"qed_table_axis": _lib.TableAxis, "qed_table_params": _lib.TableParams, "qed_species": _lib.Species,
+             "qed_fire_list": _lib.FireList, "qed_substep_opts": _lib.SubstepOpts, "qed_patch": _lib.Patch,
+             "qed_plane_wave": _lib.PlaneWave}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qed.h"', 'int main(void) {']
+    for cname, py in pairs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
