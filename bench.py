@@ -404,7 +404,9 @@ def gpu_main(args):
 
     # the evolution kernel's variants on the same workload (include/qed.h, QED_EVOLVE_*)
     variants = {}
-    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0)), ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0)),
+    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0)),
+                        ("direct_loads_4cta", (api.QED_EVOLVE_DIRECT, 0, 4)),
+                        ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0)),
                         ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0)),
                         ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2))):
         rv = time_substep(api, tabs, bufs, fire, 6, 2, ws, step0=500, shape=shape)

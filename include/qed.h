@@ -129,6 +129,10 @@ typedef struct {
     int32_t evolve_ctas_per_sm; /* CTAs per SM (1..8); 0 = the library's default / tuned   */
     int32_t evolve_pipeline; /* qed_substep's evolution kernel: QED_EVOLVE_DEFAULT, _DIRECT or
                                 _BULK (see below)                                            */
+    double qs_chi_cut;       /* leptons with chi below this neither evolve their optical depth
+                                nor emit (the cut-off a PIC code applies to photon emission,
+                                §5); 0 = off                                                  */
+    double bw_chi_cut;       /* the same for photons and pair production; 0 = off           */
 } qed_substep_opts;
 
 /* How qed_substep's evolution reads the particle arrays.  DIRECT: every thread
@@ -137,8 +141,10 @@ typedef struct {
  * tiles of every array into shared-memory stages with the bulk-copy engine,
  * consumer warps evaluate them; evolve_threads 512 (16 consumer warps, 2
  * stages) or evolve_ctas_per_sm 2 (8 warps, 2 stages) pick other shapes than
- * the default (8 consumer warps, 4 stages, 1 CTA per SM).  Both give identical
- * results.  DEFAULT is the faster of the two on GB300. */
+ * the default (8 consumer warps, 4 stages, 1 CTA per SM).  DIRECT with
+ * evolve_ctas_per_sm 4 limits the kernel to 64 registers for 4 CTAs per SM
+ * (otherwise 3).  All give identical results.  DEFAULT is DIRECT with 3 CTAs
+ * per SM, the fastest on GB300. */
 enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 
 /* ------------------------------------------------------------------------- */

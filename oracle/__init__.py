@@ -382,9 +382,11 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def evolve(proc: int, t: OracleTables, state: dict, dt: float):
+def evolve(proc: int, t: OracleTables, state: dict, dt: float, chi_cut: float = 0.0):
     """Optical-depth evolution of every particle in ``state`` (dict of arrays).
-    Returns (tau_new, chi, rate, fire)."""
+    Particles with chi < chi_cut (a cut-off applied by PIC codes, §5) take no
+    part: rate zero, optical depth unchanged, no event.  Returns (tau_new, chi,
+    rate, fire)."""
     arrs = {k: _f64(state[k]) for k in _FIELD_NAMES}
     tau = _f64(state["tau"])
     n = tau.shape[0]
@@ -393,7 +395,10 @@ def evolve(proc: int, t: OracleTables, state: dict, dt: float):
     fire = np.zeros(n, dtype=np.uint8)
     lib().oracle_evolve(proc, C.byref(t.struct), n, C.byref(f), _ptr(tau), dt, _ptr(tau_out),
                         _ptr(chi), _ptr(rate), _ptr(fire))
-    return tau_out, chi, rate, fire.astype(bool)
+    fire = fire.astype(bool)
+    below = chi < chi_cut
+    tau_out[below], rate[below], fire[below] = tau[below], 0.0, False
+    return tau_out, chi, rate, fire
 
 
 def qs_events(t: OracleTables, p: np.ndarray, chi: np.ndarray, ids: np.ndarray, seed: int,
@@ -436,7 +441,7 @@ def bw_events(t: OracleTables, p: np.ndarray, chi: np.ndarray, ids: np.ndarray, 
 
 
 def substep(t: OracleTables, species: dict, dt: float, seed: int, step: int,
-            photon_threshold: float = 0.0) -> dict:
+            photon_threshold: float = 0.0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0) -> dict:
     """One QED substep over the three species (§3, §5).
 
     ``species`` maps "electrons", "positrons", "photons" to dicts of FP64 arrays
@@ -451,7 +456,7 @@ def substep(t: OracleTables, species: dict, dt: float, seed: int, step: int,
     chis = {}
     for name, proc in (("electrons", QS), ("positrons", QS), ("photons", BW)):
         s = species[name]
-        tau_new, chi, _, f = evolve(proc, t, s, dt)
+        tau_new, chi, _, f = evolve(proc, t, s, dt, qs_chi_cut if proc == QS else bw_chi_cut)
         ns = {k: np.array(v, copy=True) for k, v in s.items()}
         ns["tau"] = tau_new
         out[name], fire[name], chis[name] = ns, f, chi

@@ -198,8 +198,11 @@ class Stats:
         return dict(zip(self.NAMES, self.t.cpu().tolist()))
 
 
-def _opts(photon_threshold=0.0, stats: Stats | None = None) -> SubstepOpts:
-    return SubstepOpts(float(photon_threshold), 0, None, stats.t.data_ptr() if stats is not None else None)
+def _opts(photon_threshold=0.0, stats: Stats | None = None, qs_chi_cut=0.0, bw_chi_cut=0.0) -> SubstepOpts:
+    o = SubstepOpts(float(photon_threshold), 0, None, stats.t.data_ptr() if stats is not None else None)
+    o.qs_chi_cut = float(qs_chi_cut)
+    o.bw_chi_cut = float(bw_chi_cut)
+    return o
 
 
 def qed_init_optical_depth(sp: SpeciesBuffers, seed: int, step: int = 0, stream=None):
@@ -237,12 +240,12 @@ class SubstepCall:
     def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                  photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
                  stats: Stats | None = None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
         self.t = t
         self.keep = (electrons, positrons, photons, fire, stats, mlp)
         self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
         self.fire = (FireList * 3)(*[f.struct() for f in fire])
-        self.opts = _opts(photon_threshold, stats)
+        self.opts = _opts(photon_threshold, stats, qs_chi_cut, bw_chi_cut)
         if mlp is not None:
             self.opts.sampler = 1
             self.opts.mlp = mlp.handle.value
@@ -261,11 +264,13 @@ class SubstepCall:
 
 def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
-                stream=None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0, ctas_per_sm: int = 0):
+                stream=None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0, ctas_per_sm: int = 0,
+                qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
     """One substep (include/qed.h).  pipeline / threads / ctas_per_sm choose the
-    evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library default)."""
+    evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library default);
+    qs_chi_cut / bw_chi_cut are the processes' chi cut-offs (0 = off)."""
     SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp, pipeline, threads,
-                ctas_per_sm)(step, stream)
+                ctas_per_sm, qs_chi_cut, bw_chi_cut)(step, stream)
 
 
 def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
@@ -395,8 +400,8 @@ def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:
 
 def make_opts(photon_threshold=0.0, stats: Stats | None = None, mlp: "Mlp | None" = None,
               d_step: torch.Tensor | None = None, evolve_threads: int = 0, evolve_ctas_per_sm: int = 0,
-              evolve_pipeline: int = 0) -> SubstepOpts:
-    o = _opts(photon_threshold, stats)
+              evolve_pipeline: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0) -> SubstepOpts:
+    o = _opts(photon_threshold, stats, qs_chi_cut, bw_chi_cut)
     if mlp is not None:
         o.sampler = 1
         o.mlp = mlp.handle.value

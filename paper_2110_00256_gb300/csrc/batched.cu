@@ -247,6 +247,7 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
     const int ctas = (o && o->evolve_ctas_per_sm) ? o->evolve_ctas_per_sm : b->ctas_per_sm;
     if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
     qed_status s = launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
+                                             o ? (T)o->qs_chi_cut : T(0), o ? (T)o->bw_chi_cut : T(0),
                                              o ? (long long *)o->d_stats : nullptr, 0, b->vec, threads, ctas, st);
     if (s) return s;
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
@@ -350,9 +351,11 @@ extern "C" qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t
                 cudaEventRecord(e0, st);
                 s = b->prec == QED_F32
                         ? launch_evolve_segments<float>((const EvolveSeg<float> *)b->d_evolve, 3 * b->n_patches,
-                                                        make_view<float>(t), 0.f, nullptr, 1, b->vec, th, c, st)
+                                                        make_view<float>(t), 0.f, 0.f, 0.f, nullptr, 1, b->vec, th,
+                                                        c, st)
                         : launch_evolve_segments<double>((const EvolveSeg<double> *)b->d_evolve, 3 * b->n_patches,
-                                                         make_view<double>(t), 0.0, nullptr, 1, b->vec, th, c, st);
+                                                         make_view<double>(t), 0.0, 0.0, 0.0, nullptr, 1, b->vec, th,
+                                                         c, st);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;

@@ -64,7 +64,7 @@ __device__ __forceinline__ void store_vec(T *p, int64_t i, const T (&in)[VEC])
 // one particle: chi, rate, optical-depth decrement; returns fire
 template <typename T>
 __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_bw, const TablesView<T> &tv,
-                                           T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T dt,
+                                           T px, T py, T pz, T ex, T ey, T ez, T bx, T by, T bz, T dt, T cut,
                                            T &tau, T &tc, T &chi_out, int &bad)
 {
     T chi, rate;
@@ -79,7 +79,7 @@ __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_b
     }
     const bool ok = isfinite(chi) && !isnan(tau) && isfinite(rate);
     bad += ok ? 0 : 1;
-    if (!ok) rate = T(0);
+    if (!ok || chi < cut) rate = T(0);  // below the process's chi threshold: no evolution
     chi_out = chi;
     if constexpr (sizeof(T) == 4) {
         // Kahan-compensated decrement; tau - tc is the optical depth
@@ -104,7 +104,7 @@ __device__ __forceinline__ void evolve_regs(const EvolveSeg<T> &sg, int64_t n, i
                                             const T (&ex)[VEC], const T (&ey)[VEC], const T (&ez)[VEC],
                                             const T (&bx)[VEC], const T (&by)[VEC], const T (&bz)[VEC], T (&tau)[VEC],
                                             T (&tc)[VEC], const T *s_qs, const T *s_bw, const TablesView<T> &tab,
-                                            T dt, long long *stats, int dry, int &bad)
+                                            T dt, T cut, long long *stats, int dry, int &bad)
 {
     const unsigned lane = threadIdx.x & 31u;
     bool fire[VEC];
@@ -114,7 +114,7 @@ __device__ __forceinline__ void evolve_regs(const EvolveSeg<T> &sg, int64_t n, i
     for (int j = 0; j < VEC; ++j) {
         T c = sizeof(T) == 4 ? tc[j] : T(0);
         fire[j] = evolve_one<T>(sg.proc, s_qs, s_bw, tab, px[j], py[j], pz[j], ex[j], ey[j], ez[j], bx[j], by[j],
-                                bz[j], dt, tau[j], c, chi[j], bad);
+                                bz[j], dt, cut, tau[j], c, chi[j], bad);
         tc[j] = c;
         fire[j] = fire[j] && (i0 + j < n);
         cnt += fire[j] ? 1 : 0;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void load_scalar(const EvolveSeg<T> &sg, int64_t n, i
 // tile index `first`, loaded straight from global memory.
 template <typename T, int VEC, int THREADS>
 __device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, long long first, const T *s_qs,
-                                            const T *s_bw, const TablesView<T> &tab, T dt, long long *stats,
+                                            const T *s_bw, const TablesView<T> &tab, T dt, T cut, long long *stats,
                                             int dry, int &bad)
 {
     const int64_t i0 = first * ((int64_t)THREADS * VEC) + (int64_t)threadIdx.x * VEC;
@@ -213,13 +213,13 @@ __device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, l
     } else {
         load_scalar<T, VEC>(sg, n, i0, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc);
     }
-    evolve_regs<T, VEC>(sg, n, i0, full, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt, stats,
-                        dry, bad);
+    evolve_regs<T, VEC>(sg, n, i0, full, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt, cut,
+                        stats, dry, bad);
 }
 
-// segments as kernel parameters (a few species)
-template <typename T, int VEC, int MAXSEG>
-__global__ void __launch_bounds__(kEvolveThreads, 3)
+// segments as kernel parameters (a few species); MINB resident CTAs per SM
+template <typename T, int VEC, int MAXSEG, int MINB = 3>
+__global__ void __launch_bounds__(kEvolveThreads, MINB)
     evolve_kernel(const __grid_constant__ EvolveArgs<T, MAXSEG> a)
 {
     __shared__ T s_qs[QED_MAX_TABLE_N];
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kEvolveThreads, 3)
         int s = 0;
         while (t >= s_end[s]) ++s;
         evolve_tile<T, VEC, kEvolveThreads>(a.seg[s], s_n[s], t - (s ? s_end[s - 1] : 0), s_qs, s_bw, a.tab, a.dt,
-                                            a.stats, 0, bad);
+                                            a.chi_cut[a.seg[s].proc], a.stats, 0, bad);
     }
     if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
 }
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[st]);
         evolve_regs<float, 4>(sg, n, i0, full4, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, a.tab,
-                              a.dt, a.stats, 0, bad);
+                              a.dt, a.chi_cut[sg.proc], a.stats, 0, bad);
     }
     if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
 }
@@ -453,8 +453,8 @@ static qed_status launch_bulk(const EvolveArgs<float, MAXSEG> &a, int64_t capaci
 // by binary search.
 template <typename T, int VEC, int THREADS>
 __global__ void __launch_bounds__(THREADS, 768 / THREADS)
-    evolve_seg_kernel(const EvolveSeg<T> *__restrict__ segs, int n_seg, TablesView<T> tab, T dt, long long *stats,
-                      int dry)
+    evolve_seg_kernel(const EvolveSeg<T> *__restrict__ segs, int n_seg, TablesView<T> tab, T dt, T cut_qs, T cut_bw,
+                      long long *stats, int dry)
 {
     __shared__ T s_qs[QED_MAX_TABLE_N];
     __shared__ T s_bw[QED_MAX_TABLE_N];
@@ -503,15 +503,16 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS)
             else
                 lo = mid + 1;
         }
-        evolve_tile<T, VEC, THREADS>(segs[lo], s_n[lo], t - (lo ? s_end[lo - 1] : 0), s_qs, s_bw, tab, dt, stats,
-                                     dry, bad);
+        const EvolveSeg<T> &sg = segs[lo];
+        evolve_tile<T, VEC, THREADS>(sg, s_n[lo], t - (lo ? s_end[lo - 1] : 0), s_qs, s_bw, tab, dt,
+                                     sg.proc == QED_PROC_QS ? cut_qs : cut_bw, stats, dry, bad);
     }
     if (stats && !dry) warp_count(stats + QED_STAT_NONFINITE, bad);
 }
 
 template <typename T, int THREADS>
-static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const TablesView<T> &tab, T dt,
-                                  long long *stats, int dry, bool vec, int ctas_per_sm, cudaStream_t st)
+static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const TablesView<T> &tab, T dt, T cut_qs,
+                                  T cut_bw, long long *stats, int dry, bool vec, int ctas_per_sm, cudaStream_t st)
 {
     const size_t dyn = (size_t)n_seg * 2 * sizeof(long long);
     int grid = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 768 / THREADS);
@@ -525,7 +526,8 @@ static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const Tab
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
             attr = true;
         }
-        evolve_seg_kernel<T, V, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
+        evolve_seg_kernel<T, V, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, cut_qs, cut_bw, stats,
+                                                                      dry);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -533,28 +535,34 @@ static qed_status launch_seg_impl(const EvolveSeg<T> *segs, int n_seg, const Tab
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
             attr = true;
         }
-        evolve_seg_kernel<T, 1, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, stats, dry);
+        evolve_seg_kernel<T, 1, THREADS><<<grid, THREADS, dyn, st>>>(segs, n_seg, tab, dt, cut_qs, cut_bw, stats,
+                                                                      dry);
     }
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
 
 template <typename T>
-qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt,
-                                  long long *stats, int dry, bool vec, int threads, int ctas_per_sm, cudaStream_t st)
+qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt, T cut_qs,
+                                  T cut_bw, long long *stats, int dry, bool vec, int threads, int ctas_per_sm,
+                                  cudaStream_t st)
 {
     if (n_seg <= 0) return QED_OK;
     switch (threads) {
-    case 128: return launch_seg_impl<T, 128>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
-    case 512: return launch_seg_impl<T, 512>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
-    default: return launch_seg_impl<T, 256>(d_segs, n_seg, tab, dt, stats, dry, vec, ctas_per_sm, st);
+    case 128:
+        return launch_seg_impl<T, 128>(d_segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry, vec, ctas_per_sm, st);
+    case 512:
+        return launch_seg_impl<T, 512>(d_segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry, vec, ctas_per_sm, st);
+    default:
+        return launch_seg_impl<T, 256>(d_segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry, vec, ctas_per_sm, st);
     }
 }
 
 template qed_status launch_evolve_segments<float>(const EvolveSeg<float> *, int, const TablesView<float> &, float,
-                                                  long long *, int, bool, int, int, cudaStream_t);
+                                                  float, float, long long *, int, bool, int, int, cudaStream_t);
 template qed_status launch_evolve_segments<double>(const EvolveSeg<double> *, int, const TablesView<double> &,
-                                                   double, long long *, int, bool, int, int, cudaStream_t);
+                                                   double, double, double, long long *, int, bool, int, int,
+                                                   cudaStream_t);
 
 // clamp the firing counters to their capacity once the evolution is done
 __global__ void clamp_fire_counts(unsigned long long *c0, int64_t cap0, unsigned long long *c1, int64_t cap1,
@@ -580,12 +588,13 @@ int sm_count()
     return g_sm_count;
 }
 
-template <typename T, int VEC, int MAXSEG>
+template <typename T, int VEC, int MAXSEG, int MINB = 3>
 static int evolve_grid(int64_t total_particles)
 {
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, evolve_kernel<T, VEC, MAXSEG>, kEvolveThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, evolve_kernel<T, VEC, MAXSEG, MINB>,
+                                                      kEvolveThreads, 0);
         if (blocks_per_sm <= 0) blocks_per_sm = 1;
     }
     const int64_t tiles = (total_particles + kEvolveTile<T, VEC> - 1) / kEvolveTile<T, VEC>;
@@ -609,8 +618,13 @@ qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t ca
     }
     if (vec_ok) {
         constexpr int V = sizeof(T) == 4 ? 4 : 2;
-        const int g = grid_override > 0 ? grid_override : evolve_grid<T, V, MAXSEG>(capacity_sum);
-        evolve_kernel<T, V, MAXSEG><<<g, kEvolveThreads, 0, st>>>(a);
+        if (sizeof(T) == 4 && ctas_per_sm == 4) {  // 64 registers: 32 warps per SM
+            const int g = grid_override > 0 ? grid_override : evolve_grid<T, V, MAXSEG, 4>(capacity_sum);
+            evolve_kernel<T, V, MAXSEG, 4><<<g, kEvolveThreads, 0, st>>>(a);
+        } else {
+            const int g = grid_override > 0 ? grid_override : evolve_grid<T, V, MAXSEG>(capacity_sum);
+            evolve_kernel<T, V, MAXSEG><<<g, kEvolveThreads, 0, st>>>(a);
+        }
     } else {
         const int g = grid_override > 0 ? grid_override : evolve_grid<T, 1, MAXSEG>(capacity_sum);
         evolve_kernel<T, 1, MAXSEG><<<g, kEvolveThreads, 0, st>>>(a);

@@ -31,6 +31,7 @@ struct EvolveArgs {
     TablesView<T> tab;
     long long *stats;
     T dt;
+    T chi_cut[2];  // per process (QED_PROC_QS, QED_PROC_BW): below it the rate is taken as zero
     int n_seg;
 };
 
@@ -46,10 +47,12 @@ template <typename T>
 bool fill_seg(EvolveSeg<T> &g, const qed_species *sp, int proc, const qed_fire_list *fire);
 
 // segments in device memory (the batched substep); threads in {128, 256, 512},
-// ctas_per_sm 0 = as many as the register budget allows; dry != 0 stores nothing
+// ctas_per_sm 0 = as many as the register budget allows; dry != 0 stores nothing;
+// cut_qs / cut_bw: chi thresholds of the two processes (rate zero below)
 template <typename T>
-qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt,
-                                  long long *stats, int dry, bool vec, int threads, int ctas_per_sm, cudaStream_t st);
+qed_status launch_evolve_segments(const EvolveSeg<T> *d_segs, int n_seg, const TablesView<T> &tab, T dt, T cut_qs,
+                                  T cut_bw, long long *stats, int dry, bool vec, int threads, int ctas_per_sm,
+                                  cudaStream_t st);
 
 qed_status check_fire(const qed_fire_list *f, const char *name);
 

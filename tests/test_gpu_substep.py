@@ -36,7 +36,7 @@ def _inputs(n, seed, tau_scale=2e-4, n_pos=None):
     return d
 
 
-def _run_gpu(api, t, host, prec, dt, seed, step, extra=3.0, threshold=0.0, caps=None):
+def _run_gpu(api, t, host, prec, dt, seed, step, extra=3.0, threshold=0.0, caps=None, cuts=(0.0, 0.0)):
     bufs, fire = {}, []
     for k in SPECIES:
         n = len(host[k]["px"])
@@ -48,18 +48,20 @@ def _run_gpu(api, t, host, prec, dt, seed, step, extra=3.0, threshold=0.0, caps=
         fire.append(api.FireBuffers(cap))
     stats = api.Stats()
     api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], dt, seed, step, fire,
-                    photon_threshold=threshold, stats=stats)
+                    photon_threshold=threshold, stats=stats, qs_chi_cut=cuts[0], bw_chi_cut=cuts[1])
     torch.cuda.synchronize()
     return {k: bufs[k].to_host() for k in SPECIES}, stats.as_dict(), fire
 
 
-def _margin_ids(ot, host64, dt, tol, seed, step):
-    """ids of particles whose decision lies within the error bound, and their children."""
+def _margin_ids(ot, host64, dt, tol, seed, step, cuts=(0.0, 0.0)):
+    """ids of particles whose decision lies within the error bound (of the
+    firing test or of a chi cut-off), and their children."""
     out = set()
     for k, proc in (("electrons", 0), ("positrons", 0), ("photons", 1)):
-        tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt)
+        tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt, cuts[proc])
         b = tau_bound(ot, proc, host64[k], chi, rate, dt, tol)
-        for pid in host64[k]["id"][np.abs(tn) <= b].tolist():
+        near_cut = np.abs(chi - cuts[proc]) <= 1e-9 * cuts[proc]
+        for pid in host64[k]["id"][(np.abs(tn) <= b) | near_cut].tolist():
             out.add(pid)
             out |= set(oracle.child_ids(seed, pid, step))
     return out
@@ -103,6 +105,28 @@ def test_substep_fp64_parity(api, tabs):
     assert ref["n_new"]["electrons"] == st["pairs"]
     excl = _margin_ids(ot, h64, 10.0, 1e-12, 99, 3)
     assert len(excl) <= 9
+    _compare(got, ref, False, 1e-12, exclude=excl)
+
+
+def test_substep_chi_cuts_fp64_parity(api, tabs):
+    """With chi cut-offs for both processes, particles below them keep their
+    optical depth bit for bit and never fire; the rest matches the oracle."""
+    ot, t = tabs
+    cuts = (15.0, 20.0)
+    host = _inputs(60_000, 13)
+    h64 = {k: as_f64(v, np.float64) for k, v in host.items()}
+    got, st, _ = _run_gpu(api, t, host, api.QED_F64, dt=10.0, seed=98, step=4, cuts=cuts)
+    ref = oracle.substep(ot, h64, dt=10.0, seed=98, step=4, qs_chi_cut=cuts[0], bw_chi_cut=cuts[1])
+    assert st["qs_events"] > 100 and st["pairs"] > 10 and st["dropped_capacity"] == 0
+    for k, proc in (("electrons", 0), ("positrons", 0), ("photons", 1)):
+        _, chi, _, f = oracle.evolve(proc, ot, h64[k], 10.0, cuts[proc])
+        below = chi < cuts[proc] * (1 - 1e-9)
+        assert 0.2 < below.mean() < 0.9 and not f[below].any()
+        g = got[k]
+        n = len(h64[k]["id"])
+        assert np.array_equal(g["id"][:n], h64[k]["id"])
+        assert np.array_equal(g["tau"][:n][below], h64[k]["tau"][below])
+    excl = _margin_ids(ot, h64, 10.0, 1e-12, 98, 4, cuts)
     _compare(got, ref, False, 1e-12, exclude=excl)
 
 
@@ -239,7 +263,8 @@ def test_bulk_copy_pipeline_equals_direct_loads(api, tabs, shape):
     the same bits as the one with direct 16-byte loads: the same particles
     fire with the same chi, and every particle (secondaries included) ends
     identical.  Sizes give full tiles, a ragged tail, and a species smaller
-    than one tile."""
+    than one tile.  Every destination has room for every event (which events
+    run when one fills up depends on the order of the firing list)."""
     _, t = tabs
     threads, ctas = shape
     host = _inputs(50_003, 41, n_pos=1000)
@@ -249,7 +274,7 @@ def test_bulk_copy_pipeline_equals_direct_loads(api, tabs, shape):
         bufs, fire = {}, []
         for k in SPECIES:
             n = len(host[k]["px"])
-            b = api.SpeciesBuffers(3 * n + 64, api.QED_F32)
+            b = api.SpeciesBuffers(n + 130_000, api.QED_F32)
             b.set(host[k])
             bufs[k] = b
             fire.append(api.FireBuffers(b.capacity))
@@ -264,7 +289,8 @@ def test_bulk_copy_pipeline_equals_direct_loads(api, tabs, shape):
             fl.append((i[o], c[o]))
         out[pipe] = ({k: sort_by_id(bufs[k].to_host()) for k in SPECIES}, stats.as_dict(), fl)
     (da, sa, fa), (db, sb, fb) = out[api.QED_EVOLVE_DIRECT], out[api.QED_EVOLVE_BULK]
-    assert sa == sb and sb["wait_timeout"] == 0 and sb["qs_events"] > 100 and sb["pairs"] > 10
+    assert sa == sb and sb["wait_timeout"] == 0 and sb["dropped_capacity"] == 0
+    assert sb["qs_events"] > 100 and sb["pairs"] > 10
     for (ia, ca), (ib, cb) in zip(fa, fb):
         assert np.array_equal(ia, ib) and np.array_equal(ca, cb)
     for k in SPECIES:

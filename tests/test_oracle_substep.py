@@ -300,3 +300,24 @@ def test_substep_conserves_energy_and_bookkeeping(oracle_tables_small):
     # every optical depth left is positive
     for name in ("electrons", "positrons", "photons"):
         assert np.all(out[name]["tau"] > 0)
+
+
+def test_chi_cut_special_cases(oracle_tables_small):
+    """A chi cut-off of 0 changes nothing; one above every particle's chi
+    freezes every optical depth; in between, exactly the particles below it
+    are frozen and the rest evolve as without a cut."""
+    from paper_2110_00256_gb300 import workloads
+    ot = oracle_tables_small
+    h = {k: np.asarray(v, dtype=np.float64) if k != "id" else v
+         for k, v in workloads.paper_benchmark(5000, 3, 0).items()}
+    h["tau"] = h["tau"] * 1e-3
+    t0, chi0, r0, f0 = oracle.evolve(0, ot, h, 10.0)
+    t1, chi1, r1, f1 = oracle.evolve(0, ot, h, 10.0, 0.0)
+    assert np.array_equal(t0, t1) and np.array_equal(f0, f1) and f0.any()
+    t2, _, r2, f2 = oracle.evolve(0, ot, h, 10.0, 10 * chi0.max())
+    assert np.array_equal(t2, h["tau"]) and not f2.any() and not r2.any()
+    cut = np.median(chi0)
+    t3, _, r3, f3 = oracle.evolve(0, ot, h, 10.0, cut)
+    lo = chi0 < cut
+    assert np.array_equal(t3[lo], h["tau"][lo]) and not f3[lo].any()
+    assert np.array_equal(t3[~lo], t0[~lo]) and np.array_equal(f3[~lo], f0[~lo]) and np.array_equal(r3[~lo], r0[~lo])
