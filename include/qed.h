@@ -307,6 +307,13 @@ qed_status qed_push_plane_wave(const qed_species *sp, double charge, const qed_p
  * t0 + step * dt, the step read from d_step when it is not NULL. */
 qed_status qed_push_batched(const qed_batch *b, const qed_plane_wave *wave, double t0, double dt,
                             int64_t step, const int64_t *d_step, void *stream);
+/* One step of dt for every particle of `sp` (positions required) in the fields
+ * already stored in its E and B arrays (uniform static fields, or fields a PIC
+ * code gathered at the particles): Boris push for charge -1 or +1, straight
+ * flight for charge 0, then x += v dt.  The fields are not changed; products of
+ * the substep inherit their parent's, so a uniform field stays set. */
+qed_status qed_push_stored_fields(const qed_species *sp, double charge, double dt, qed_precision prec,
+                                  void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* learned sampler (stands in for the 2-D tables of §3.1, §3.2)              */

@@ -99,6 +99,7 @@ SIGNATURES = {
     "qed_substep_batched": (_S, [_P, _P, _D, _U64, _I64, C.POINTER(SubstepOpts), _P]),
     "qed_tune_evolve": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float), _P]),
     "qed_push_plane_wave": (_S, [C.POINTER(Species), _D, C.POINTER(PlaneWave), _D, _D, _S, _P]),
+    "qed_push_stored_fields": (_S, [C.POINTER(Species), _D, _D, _S, _P]),
     "qed_push_batched": (_S, [_P, C.POINTER(PlaneWave), _D, _D, _I64, _P, _P]),
     "qed_mlp_create": (_S, [_P, _U64, C.POINTER(_P), _P]),
     "qed_mlp_destroy": (_S, [_P]),

@@ -23,7 +23,7 @@ __all__ = [
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
-    "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave",
+    "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields",
     "qed_push_batched",
 ]
 
@@ -424,6 +424,11 @@ def qed_push_plane_wave(sp: SpeciesBuffers, charge: float, wave, t: float, dt: f
     s = sp.struct()
     check(lib().qed_push_plane_wave(C.byref(s), float(charge), C.byref(wave), float(t), float(dt), sp.prec,
                                     _stream(stream)))
+
+
+def qed_push_stored_fields(sp: SpeciesBuffers, charge: float, dt: float, stream=None):
+    s = sp.struct()
+    check(lib().qed_push_stored_fields(C.byref(s), float(charge), float(dt), sp.prec, _stream(stream)))
 
 
 def qed_push_batched(b: Batch, wave, t0: float, dt: float, step: int = 0, d_step: torch.Tensor | None = None,

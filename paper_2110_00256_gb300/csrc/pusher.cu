@@ -1,6 +1,6 @@
-// pusher.cu -- a minimal particle push in an analytic plane wave, to drive the
-// QED substep in a cascade (the paper's substep runs inside a PIC code; this
-// is not from the paper).  Units: c = m_e = 1, momentum in m_e c, fields in E_s
+// pusher.cu -- a minimal particle push, in an analytic plane wave or in the
+// fields stored with the particles, to drive the QED substep in a cascade (the
+// paper's substep runs inside a PIC code; this is not from the paper).  Units: c = m_e = 1, momentum in m_e c, fields in E_s
 // and E_s / c, time in hbar/(m_e c^2), lengths in hbar/(m_e c); dp/dt =
 // q (E + v x B).  Positions at t_n, momenta at t_{n+1/2}: fields at (x_n, t_n)
 // are written into the species' field arrays (where the substep reads them),
@@ -38,13 +38,11 @@ __device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, 
     bz = d * ey;
 }
 
+// momentum (Boris) and position update of particle i with the fields (ex .. bz)
 template <typename T>
-__device__ __forceinline__ void push_one(const PushSeg<T> &g, int64_t i, const WaveParams &w, double t, T dt)
+__device__ __forceinline__ void advance(const PushSeg<T> &g, int64_t i, T x, T ex, T ey, T ez, T bx, T by, T bz,
+                                        T dt)
 {
-    const T x = g.x[i];
-    T ex, ey, ez, bx, by, bz;
-    wave_fields<T>(w, t, x, ex, ey, ez, bx, by, bz);
-    g.ex[i] = ex, g.ey[i] = ey, g.ez[i] = ez, g.bx[i] = bx, g.by[i] = by, g.bz[i] = bz;
     T px = g.px[i], py = g.py[i], pz = g.pz[i];
     T vx, vy, vz;
     if (g.q == T(0)) {
@@ -69,6 +67,17 @@ __device__ __forceinline__ void push_one(const PushSeg<T> &g, int64_t i, const W
     g.x[i] = x + vx * dt;
     g.y[i] = g.y[i] + vy * dt;
     g.z[i] = g.z[i] + vz * dt;
+}
+
+// plane wave: fields at (x_n, t_n) are written into the species, then the step
+template <typename T>
+__device__ __forceinline__ void push_one(const PushSeg<T> &g, int64_t i, const WaveParams &w, double t, T dt)
+{
+    const T x = g.x[i];
+    T ex, ey, ez, bx, by, bz;
+    wave_fields<T>(w, t, x, ex, ey, ez, bx, by, bz);
+    g.ex[i] = ex, g.ey[i] = ey, g.ez[i] = ez, g.bx[i] = bx, g.by[i] = by, g.bz[i] = bz;
+    advance<T>(g, i, x, ex, ey, ez, bx, by, bz, dt);
 }
 
 template <typename T>
@@ -145,6 +154,16 @@ __global__ void __launch_bounds__(256) push_single_kernel(const __grid_constant_
         push_one<T>(g, i, w, t, (T)dt);
 }
 
+// fields already stored in the species (uniform fields, or gathered by the caller)
+template <typename T>
+__global__ void __launch_bounds__(256) push_stored_kernel(const __grid_constant__ PushSeg<T> g, double dt)
+{
+    int64_t n = *g.count;
+    n = n < 0 ? 0 : (n > g.cap ? g.cap : n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        advance<T>(g, i, g.x[i], g.ex[i], g.ey[i], g.ez[i], g.bx[i], g.by[i], g.bz[i], (T)dt);
+}
+
 template <typename T>
 qed_status launch_push(const void *d_segs, int n_seg, const WaveParams &w, double t0, double dt,
                        const int64_t *d_step, int64_t step, int64_t capacity, cudaStream_t st)
@@ -204,6 +223,27 @@ extern "C" qed_status qed_push_plane_wave(const qed_species *sp, double charge, 
         push_single_kernel<float><<<(int)grid, 256, 0, st>>>(push_seg<float>(sp, charge), wave_params(wave), t, dt);
     else
         push_single_kernel<double><<<(int)grid, 256, 0, st>>>(push_seg<double>(sp, charge), wave_params(wave), t, dt);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+extern "C" qed_status qed_push_stored_fields(const qed_species *sp, double charge, double dt, qed_precision prec,
+                                             void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_species(sp, "species", prec))) return s;
+    if (!sp->x || !sp->y || !sp->z) QED_FAIL(QED_ERR_INVALID_ARG, "the push needs the species' positions");
+    if (!std::isfinite(charge)) QED_FAIL(QED_ERR_INVALID_ARG, "charge must be finite");
+    if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    cudaStream_t st = as_stream(stream);
+    int64_t grid = (sp->capacity + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
+    if (prec == QED_F32)
+        push_stored_kernel<float><<<(int)grid, 256, 0, st>>>(push_seg<float>(sp, charge), dt);
+    else
+        push_stored_kernel<double><<<(int)grid, 256, 0, st>>>(push_seg<double>(sp, charge), dt);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }

@@ -160,3 +160,41 @@ def test_cascade_conserves_light_front_momentum(api):
     assert s["qs_events"] > 4 * n and s["dropped_capacity"] == 0 and s["nonfinite"] == 0
     lf1 = light_front()
     assert lf1 == pytest.approx(lf0, rel=1e-3), (lf0, lf1, s)
+
+
+@pytest.mark.parametrize("charge", [-1.0, 1.0, 0.0])
+def test_push_stored_fields_fp64_matches_oracle(api, charge):
+    """Boris push in the fields stored with the particles (here random, a
+    different field per particle), 30 steps, against oracle/pusher.boris; the
+    fields are left untouched."""
+    n = 4000
+    r = np.random.default_rng(8)
+    sp = _species(api, n, api.QED_F64, 9)
+    E = r.uniform(-1e-3, 1e-3, (n, 3))
+    B = r.uniform(-1e-3, 1e-3, (n, 3))
+    h = sp.to_host()
+    h.update({c: E[:, i] for i, c in enumerate(("ex", "ey", "ez"))})
+    h.update({c: B[:, i] for i, c in enumerate(("bx", "by", "bz"))})
+    sp.set(h)
+    pos = np.stack([h["x"], h["y"], h["z"]], 1)
+    p = np.stack([h["px"], h["py"], h["pz"]], 1)
+    dt = 500.0
+    for _ in range(30):
+        api.qed_push_stored_fields(sp, charge, dt)
+        if charge == 0:
+            v = p / np.linalg.norm(p, axis=1, keepdims=True)
+        else:
+            p = opush.boris(p, E, B, charge, dt)
+            v = p / np.sqrt(1 + np.sum(p * p, axis=1, keepdims=True))
+        pos = pos + v * dt
+    torch.cuda.synchronize()
+    g = sp.to_host()
+    scale = np.linalg.norm(p, axis=1)
+    for i, c in enumerate(("px", "py", "pz")):
+        assert np.all(np.abs(g[c] - p[:, i]) <= 1e-11 * scale), c
+    for i, c in enumerate(("x", "y", "z")):
+        assert np.allclose(g[c], pos[:, i], rtol=1e-12, atol=1e-6), c
+    for i, c in enumerate(("ex", "ey", "ez")):
+        assert np.array_equal(g[c], E[:, i]), c
+    for i, c in enumerate(("bx", "by", "bz")):
+        assert np.array_equal(g[c], B[:, i]), c
