@@ -195,11 +195,11 @@ def counts(bufs):
     return sum(int(bufs[k].count.item()) for k in ("electrons", "positrons", "photons"))
 
 
-def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None, shape=(0, 0, 0)):
+def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None, shape=(0, 0, 0, 0)):
     import torch
     stats = api.Stats()
     call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats,
-                           mlp=mlp, pipeline=shape[0], threads=shape[1], ctas_per_sm=shape[2])
+                           mlp=mlp, pipeline=shape[0], threads=shape[1], ctas_per_sm=shape[2], prefetch=shape[3])
     for s in range(warmup):
         call(step0 + s)
     torch.cuda.synchronize()
@@ -404,11 +404,15 @@ def gpu_main(args):
 
     # the evolution kernel's variants on the same workload (include/qed.h, QED_EVOLVE_*)
     variants = {}
-    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0)),
-                        ("direct_loads_4cta", (api.QED_EVOLVE_DIRECT, 0, 4)),
-                        ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0)),
-                        ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0)),
-                        ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2))):
+    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0, 0)),
+                        ("direct_loads_4cta", (api.QED_EVOLVE_DIRECT, 0, 4, 0)),
+                        ("direct_l2_prefetch_1", (api.QED_EVOLVE_DIRECT, 0, 0, 1)),
+                        ("direct_l2_prefetch_2", (api.QED_EVOLVE_DIRECT, 0, 0, 2)),
+                        ("direct_l2_prefetch_4", (api.QED_EVOLVE_DIRECT, 0, 0, 4)),
+                        ("direct_4cta_l2_prefetch_1", (api.QED_EVOLVE_DIRECT, 0, 4, 1)),
+                        ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0, 0)),
+                        ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0, 0)),
+                        ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2, 0))):
         rv = time_substep(api, tabs, bufs, fire, 6, 2, ws, step0=500, shape=shape)
         evm = sum(rv["evolve_ms"]) / len(rv["evolve_ms"])
         variants[name] = {"evolve_ms": round(evm, 4), "hbm_gbs": round(BYTES_F32 * rv["n_before"] / (evm * 1e-3) / 1e9, 1),

@@ -133,6 +133,8 @@ typedef struct {
                                 nor emit (the cut-off a PIC code applies to photon emission,
                                 §5); 0 = off                                                  */
     double bw_chi_cut;       /* the same for photons and pair production; 0 = off           */
+    int32_t evolve_prefetch; /* DIRECT evolution of qed_substep: each CTA asks L2 for the tile
+                                it will read this many rounds ahead (0 = none, up to 8)      */
 } qed_substep_opts;
 
 /* How qed_substep's evolution reads the particle arrays.  DIRECT: every thread

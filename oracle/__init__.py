@@ -90,6 +90,8 @@ def lib():
             "oracle_qs_cdf": (_D, [_D, _D]),
             "oracle_bw_cdf": (_D, [_D, _D]),
             "oracle_qs_cdf_sorted": (None, [_D, _I64, _P, _P]),
+            "oracle_qs_S_array": (None, [_D, _I64, _P, _P]),
+            "oracle_bw_bracket_array": (None, [_D, _I64, _P, _P]),
             "oracle_bw_cdf_sorted": (None, [_D, _I64, _P, _P]),
             "oracle_build_qs_tables": (None, [_D, _D, C.c_int, C.c_int, _D, _P, _P]),
             "oracle_build_bw_tables": (None, [_D, _D, C.c_int, C.c_int, _P, _P]),
@@ -216,6 +218,22 @@ def bw_cdf_sorted(chig: float, xs) -> np.ndarray:
     assert np.all(np.diff(xs) >= 0)
     out = np.zeros(xs.shape[0])
     lib().oracle_bw_cdf_sorted(chig, xs.shape[0], _ptr(xs), _ptr(out))
+    return out
+
+
+def qs_S_array(chi: float, xs) -> np.ndarray:
+    """S(chi, xi) of Eq. (qs_diff_cross) at every point of xs."""
+    xs = _f64(xs)
+    out = np.zeros(xs.shape[0])
+    lib().oracle_qs_S_array(chi, xs.shape[0], _ptr(xs), _ptr(out))
+    return out
+
+
+def bw_bracket_array(chig: float, xs) -> np.ndarray:
+    """The bracket of Eq. (t_func_0) at every point of xs (xi = chi_-/chi_gamma)."""
+    xs = _f64(xs)
+    out = np.zeros(xs.shape[0])
+    lib().oracle_bw_bracket_array(chig, xs.shape[0], _ptr(xs), _ptr(out))
     return out
 
 

@@ -300,3 +300,18 @@ void oracle_bw_cdf_sorted(double chig, int64_t n, const double *xs, double *out)
         out[i] = acc / (2.0 * half);
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* pointwise spectra on many points (the kinetic-equation reference)          */
+/* ------------------------------------------------------------------------- */
+void oracle_qs_S_array(double chi, int64_t n, const double *xi, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_qs_S(chi, xi[i]);
+}
+
+void oracle_bw_bracket_array(double chig, int64_t n, const double *xi, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_bw_bracket(chig, xi[i]);
+}

@@ -65,7 +65,8 @@ class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
                 ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
                 ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32),
-                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double)]
+                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double),
+                ("evolve_prefetch", C.c_int32)]
 
 
 _P = C.c_void_p

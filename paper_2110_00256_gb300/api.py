@@ -240,7 +240,7 @@ class SubstepCall:
     def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                  photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
                  stats: Stats | None = None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0,
-                 ctas_per_sm: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
+                 ctas_per_sm: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0, prefetch: int = 0):
         self.t = t
         self.keep = (electrons, positrons, photons, fire, stats, mlp)
         self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
@@ -252,6 +252,7 @@ class SubstepCall:
         self.opts.evolve_pipeline = int(pipeline)
         self.opts.evolve_threads = int(threads)
         self.opts.evolve_ctas_per_sm = int(ctas_per_sm)
+        self.opts.evolve_prefetch = int(prefetch)
         self.dt = float(dt)
         self.seed = int(seed)
         self.prec = electrons.prec
@@ -265,12 +266,12 @@ class SubstepCall:
 def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
                 stream=None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0, ctas_per_sm: int = 0,
-                qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
-    """One substep (include/qed.h).  pipeline / threads / ctas_per_sm choose the
-    evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library default);
-    qs_chi_cut / bw_chi_cut are the processes' chi cut-offs (0 = off)."""
+                qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0, prefetch: int = 0):
+    """One substep (include/qed.h).  pipeline / threads / ctas_per_sm / prefetch
+    choose the evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library
+    default); qs_chi_cut / bw_chi_cut are the processes' chi cut-offs (0 = off)."""
     SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp, pipeline, threads,
-                ctas_per_sm, qs_chi_cut, bw_chi_cut)(step, stream)
+                ctas_per_sm, qs_chi_cut, bw_chi_cut, prefetch)(step, stream)
 
 
 def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,

@@ -217,7 +217,29 @@ __device__ __forceinline__ void evolve_tile(const EvolveSeg<T> &sg, int64_t n, l
                         stats, dry, bad);
 }
 
-// segments as kernel parameters (a few species); MINB resident CTAs per SM
+// the k-th streamed array of a segment: px .. bz, tau, tau_c
+template <typename T>
+__device__ __forceinline__ const T *seg_array(const EvolveSeg<T> &g, int k)
+{
+    switch (k) {
+    case 0: return g.px;
+    case 1: return g.py;
+    case 2: return g.pz;
+    case 3: return g.ex;
+    case 4: return g.ey;
+    case 5: return g.ez;
+    case 6: return g.bx;
+    case 7: return g.by;
+    case 8: return g.bz;
+    case 9: return g.tau;
+    default: return g.tau_c;
+    }
+}
+
+// segments as kernel parameters (a few species); MINB resident CTAs per SM.
+// a.prefetch > 0 (16-byte-aligned arrays): at every tile, lanes of the first
+// warp ask L2 for this CTA's tile a.prefetch rounds ahead, one bulk prefetch
+// per array, so that more of the stream is in flight than the loads alone keep.
 template <typename T, int VEC, int MAXSEG, int MINB = 3>
 __global__ void __launch_bounds__(kEvolveThreads, MINB)
     evolve_kernel(const __grid_constant__ EvolveArgs<T, MAXSEG> a)
@@ -242,8 +264,20 @@ __global__ void __launch_bounds__(kEvolveThreads, MINB)
     }
     __syncthreads();
     const long long total = a.n_seg ? s_end[a.n_seg - 1] : 0;
+    constexpr int kArrays = sizeof(T) == 4 ? 11 : 10;
     int bad = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        if (VEC > 1 && a.prefetch > 0 && threadIdx.x < kArrays) {
+            const long long tn = t + (long long)a.prefetch * gridDim.x;
+            if (tn < total) {
+                int sn = 0;
+                while (tn >= s_end[sn]) ++sn;
+                const int64_t i0 = (tn - (sn ? s_end[sn - 1] : 0)) * tile;
+                const int64_t len = s_n[sn] - i0 < tile ? s_n[sn] - i0 : tile;
+                const uint32_t bytes = (uint32_t)(len * (int64_t)sizeof(T)) & ~15u;
+                if (bytes) l2_prefetch_bulk(seg_array<T>(a.seg[sn], threadIdx.x) + i0, bytes);
+            }
+        }
         int s = 0;
         while (t >= s_end[s]) ++s;
         evolve_tile<T, VEC, kEvolveThreads>(a.seg[s], s_n[s], t - (s ? s_end[s - 1] : 0), s_qs, s_bw, a.tab, a.dt,
@@ -265,23 +299,6 @@ __global__ void __launch_bounds__(kEvolveThreads, MINB)
 // keep S - 1 tiles of every SM's stream in flight while one is evaluated.
 // ---------------------------------------------------------------------------
 constexpr int kBulkArrays = 11;
-
-__device__ __forceinline__ const float *bulk_src(const EvolveSeg<float> &g, int k)
-{
-    switch (k) {
-    case 0: return g.px;
-    case 1: return g.py;
-    case 2: return g.pz;
-    case 3: return g.ex;
-    case 4: return g.ey;
-    case 5: return g.ez;
-    case 6: return g.bx;
-    case 7: return g.by;
-    case 8: return g.bz;
-    case 9: return g.tau;
-    default: return g.tau_c;
-    }
-}
 
 // bounded wait that also gives up as soon as another warp has given up
 __device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
@@ -357,7 +374,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
                 if (lane == 0) mbar_arrive_expect_tx(&s_full[st], kBulkArrays * TP * (uint32_t)sizeof(float));
                 __syncwarp();
                 if (lane < kBulkArrays)
-                    bulk_g2s(s_stage + ((size_t)st * kBulkArrays + lane) * TP, bulk_src(a.seg[s], lane) + i0,
+                    bulk_g2s(s_stage + ((size_t)st * kBulkArrays + lane) * TP, seg_array<float>(a.seg[s], lane) + i0,
                              TP * (uint32_t)sizeof(float), &s_full[st], pol);
             } else if (lane == 0) {
                 mbar_arrive(&s_full[st]);

@@ -1,0 +1,73 @@
+"""Many-step runs of the whole library (push + substep, ~1000 steps) on the
+three test cases of Ridgers et al. (2014) that §5 of the paper reproduces,
+against the kinetic-equation spectra of the oracle (tests/golden/
+ridgers_kinetic.json, written by tests/golden/make_ridgers_reference.py): the
+primary electrons', the photons' and the pairs' energy spectra, in FP32 and in
+FP64 (§5: FP32 does not degrade the spectra)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+N = 100_000
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2110_00256_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def reference():
+    with open(os.path.join(HERE, "golden", "ridgers_kinetic.json")) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def tables(api):
+    return api.qed_tables_generate(api.table_params())
+
+
+def _counts(x, edges):
+    """histogram on the reference's edges, plus everything below the first"""
+    h, _ = np.histogram(x, bins=edges)
+    return np.concatenate([h, [np.sum(x < edges[0])]]).astype(np.float64)
+
+
+def _check(name, x, edges, dens, n, overdispersion, min_expected=200.0, rel=0.03):
+    """every bin with enough expected entries within 5 sigma (sigma^2 =
+    overdispersion x expected) plus `rel` of the expectation"""
+    got = _counts(x, np.asarray(edges))
+    exp = n * np.asarray(dens)
+    m = exp >= min_expected
+    assert m.sum() >= 10, name
+    dev = np.abs(got[m] - exp[m])
+    tol = 5.0 * np.sqrt(overdispersion * exp[m]) + rel * exp[m]
+    worst = float(np.max(dev / tol))
+    assert worst <= 1.0, (name, worst, got[m], exp[m])
+    return worst
+
+
+@pytest.mark.parametrize("prec_name", ["f32", "f64"])
+@pytest.mark.parametrize("case", [1, 2, 3])
+def test_ridgers_spectra_match_kinetic_equation(api, tables, reference, case, prec_name):
+    from paper_2110_00256_gb300 import ridgers
+    prec = api.QED_F32 if prec_name == "f32" else api.QED_F64
+    ref = reference["cases"][str(case)]
+    out = ridgers.run(tables, case, N, prec)
+    st = out["stats"]
+    assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0 and st["fire_overflow"] == 0
+    assert out["primary"].shape[0] == N
+    w = {"primary": _check("primary", out["primary"], ref["lepton_edges"], ref["primary"], N, 1.0),
+         "photons": _check("photons", out["photons"], ref["photon_edges"], ref["photons"], N, 3.0)}
+    mean = float(np.mean(1.0 + out["primary"]))
+    assert mean == pytest.approx(ref["mean_gamma_primary"], rel=5e-3)
+    if case == 3:  # pairs are only plentiful at chi = 9
+        w["secondary"] = _check("secondary", out["secondary"], ref["lepton_edges"], ref["secondary"], N, 3.0)
+    print(case, prec_name, w, "mean gamma", mean, ref["mean_gamma_primary"], st)

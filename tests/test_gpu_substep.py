@@ -257,38 +257,42 @@ def test_full_size_fp32_workload_sampled(api, tabs):
         assert f.sum() > 0
 
 
-@pytest.mark.parametrize("shape", [(0, 0), (512, 0), (0, 2)], ids=["8w4s", "16w2s", "8w2sx2"])
-def test_bulk_copy_pipeline_equals_direct_loads(api, tabs, shape):
-    """The evolution with tiles staged in shared memory by bulk copies gives
-    the same bits as the one with direct 16-byte loads: the same particles
-    fire with the same chi, and every particle (secondaries included) ends
-    identical.  Sizes give full tiles, a ragged tail, and a species smaller
-    than one tile.  Every destination has room for every event (which events
-    run when one fills up depends on the order of the firing list)."""
+@pytest.mark.parametrize("variant", [(2, 0, 0, 0), (2, 512, 0, 0), (2, 0, 2, 0), (1, 0, 4, 0), (1, 0, 0, 1),
+                                     (1, 0, 0, 3), (1, 0, 4, 2)],
+                         ids=["bulk8w4s", "bulk16w2s", "bulk8w2sx2", "direct4cta", "direct_pf1", "direct_pf3",
+                              "direct4cta_pf2"])
+def test_evolution_variants_equal_direct_loads(api, tabs, variant):
+    """Every variant of the evolution kernel (bulk copies into shared memory,
+    four CTAs per SM, L2 prefetch ahead) gives the same bits as the default
+    direct loads: the same particles fire with the same chi, and every particle
+    (secondaries included) ends identical.  Sizes give full tiles, a ragged
+    tail, and a species smaller than one tile.  Every destination has room for
+    every event (which events run when one fills up depends on the order of the
+    firing list)."""
     _, t = tabs
-    threads, ctas = shape
-    host = _inputs(50_003, 41, n_pos=1000)
+    pipe_v, threads, ctas, pf = variant
+    host = _inputs(600_003, 41, n_pos=1000)  # more tiles than the grid has CTAs (prefetch ahead)
     host["photons"] = _inputs(70_001, 42)["photons"]
     out = {}
-    for pipe in (api.QED_EVOLVE_DIRECT, api.QED_EVOLVE_BULK):
+    for key, (pipe, th, ct, p) in (("ref", (api.QED_EVOLVE_DIRECT, 0, 0, 0)), ("var", (pipe_v, threads, ctas, pf))):
         bufs, fire = {}, []
         for k in SPECIES:
             n = len(host[k]["px"])
-            b = api.SpeciesBuffers(n + 130_000, api.QED_F32)
+            b = api.SpeciesBuffers(n + 700_000, api.QED_F32)
             b.set(host[k])
             bufs[k] = b
             fire.append(api.FireBuffers(b.capacity))
         stats = api.Stats()
         api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 5, 2, fire, stats=stats,
-                        pipeline=pipe, threads=threads, ctas_per_sm=ctas)
+                        pipeline=pipe, threads=th, ctas_per_sm=ct, prefetch=p)
         torch.cuda.synchronize()
         fl = []
         for f in fire:
             i, c = f.idx[:f.n()].cpu().numpy(), f.chi[:f.n()].cpu().numpy()
             o = np.argsort(i)
             fl.append((i[o], c[o]))
-        out[pipe] = ({k: sort_by_id(bufs[k].to_host()) for k in SPECIES}, stats.as_dict(), fl)
-    (da, sa, fa), (db, sb, fb) = out[api.QED_EVOLVE_DIRECT], out[api.QED_EVOLVE_BULK]
+        out[key] = ({k: sort_by_id(bufs[k].to_host()) for k in SPECIES}, stats.as_dict(), fl)
+    (da, sa, fa), (db, sb, fb) = out["ref"], out["var"]
     assert sa == sb and sb["wait_timeout"] == 0 and sb["dropped_capacity"] == 0
     assert sb["qs_events"] > 100 and sb["pairs"] > 10
     for (ia, ca), (ib, cb) in zip(fa, fb):
