@@ -21,9 +21,9 @@ The number densities f then obey d f / dt = A f with A built from these rates
 and spectra; f(t) = exp(A t) f(0).
 
 Discretisation: log-spaced energy bins; a particle sits at its bin's centre and
-a jump by d (in ln energy) is shared between the two bins whose centres bracket
-the landing point, with linear weights (this keeps the mean log-energy shift of
-every jump exact, so many small emissions drift the lepton correctly).  The
+the landing point of a jump is shared between the two bins whose centres
+bracket it, with weights linear in energy (this keeps the energy of every jump
+exact, so that many small emissions drift the lepton correctly).  The
 spectra are integrated on fine grids from the oracle's pointwise S and the
 bracket of Eq. (t_func_0), so the rates are the oracle's exact G and T (not the
 tables).  Three populations: the primary leptons, the photons, and the
@@ -98,17 +98,22 @@ class LogBins:
 
     def share(self, ln_e: np.ndarray, mass: np.ndarray) -> np.ndarray:
         """Distribute `mass` landing at ln energies `ln_e` over the n bins and an
-        underflow bin (index n): returns an array of n + 1."""
+        underflow bin (index n): returns an array of n + 1.  A landing point
+        between two centres is shared linearly in energy, which keeps the
+        energy of every jump."""
         pos = (ln_e - math.log(self.centres[0])) / self.d
         out = np.zeros(self.n + 1)
         under = pos < 0.0
         out[self.n] += mass[under].sum()
-        pos, m = np.minimum(pos[~under], self.n - 1), mass[~under]
+        top = pos >= self.n - 1
+        out[self.n - 1] += mass[top & ~under].sum()
+        keep = ~under & ~top
+        pos, m, e = pos[keep], mass[keep], np.exp(ln_e[keep])
         i0 = np.floor(pos).astype(np.int64)
-        fr = pos - i0
-        i1 = np.minimum(i0 + 1, self.n - 1)
+        lo, hi = self.centres[i0], self.centres[i0 + 1]
+        fr = (e - lo) / (hi - lo)
         np.add.at(out, i0, m * (1.0 - fr))
-        np.add.at(out, i1, m * fr)
+        np.add.at(out, i0 + 1, m * fr)
         return out
 
 

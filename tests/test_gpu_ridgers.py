@@ -46,7 +46,7 @@ def _check(name, x, edges, dens, n, overdispersion, min_expected=200.0, rel=0.03
     got = _counts(x, np.asarray(edges))
     exp = n * np.asarray(dens)
     m = exp >= min_expected
-    assert m.sum() >= 10, name
+    assert m.sum() >= 6, name
     dev = np.abs(got[m] - exp[m])
     tol = 5.0 * np.sqrt(overdispersion * exp[m]) + rel * exp[m]
     worst = float(np.max(dev / tol))
