@@ -117,6 +117,8 @@ def lib():
             "oracle_rates": (None, [C.c_int, C.POINTER(Tables), _I64, _P, _P, _P]),
             "oracle_qs_table_cdf": (_D, [C.POINTER(Tables), _D, _D]),
             "oracle_bw_table_cdf": (_D, [C.POINTER(Tables), _D, _D]),
+            "oracle_qs_table_cdf_array": (None, [C.POINTER(Tables), _D, _I64, _P, _P]),
+            "oracle_bw_table_cdf_array": (None, [C.POINTER(Tables), _D, _I64, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -320,6 +322,18 @@ class OracleTables:
     def bw_table_cdf(self, chig, xi):
         """r in [0, 1/2] that the BW table lookup maps to xi in [0, 1/2]."""
         return lib().oracle_bw_table_cdf(C.byref(self.struct), chig, xi)
+
+    def qs_table_cdf_array(self, chi, xs):
+        xs = _f64(xs)
+        out = np.zeros(xs.shape[0])
+        lib().oracle_qs_table_cdf_array(C.byref(self.struct), chi, xs.shape[0], _ptr(xs), _ptr(out))
+        return out
+
+    def bw_table_cdf_array(self, chig, xs):
+        xs = _f64(xs)
+        out = np.zeros(xs.shape[0])
+        lib().oracle_bw_table_cdf_array(C.byref(self.struct), chig, xs.shape[0], _ptr(xs), _ptr(out))
+        return out
 
     def qs_sample_xi(self, chi, r):
         return lib().oracle_qs_sample_xi(C.byref(self.struct), chi, r)

@@ -130,12 +130,53 @@ def _mid(xi):
 
 
 # ----------------------------------------------------------------------------
+# the two models: the exact spectra, or the tabulated method (§3.1, §3.2)
+# ----------------------------------------------------------------------------
+class ExactModel:
+    """Rates and spectra of §2 from the oracle's quadrature."""
+
+    def qs(self, chi: float, gamma: float):
+        xi, cdf, G = qs_spectrum(chi)
+        return xi, cdf, (2.0 / 3.0) * ALPHA_F * G / gamma
+
+    def bw(self, chig: float, g: float):
+        xi, cdf, T = bw_spectrum(chig)
+        return xi, cdf, (ALPHA_F * chig * T / g if T > 0.0 else 0.0)
+
+
+class TableModel:
+    """What the substep samples with tables `t` (an OracleTables): the rates
+    from the 1-D tables (with their out-of-table rules) and, as the spectra,
+    the forward maps of the inverse-CDF lookups on the 2-D tables."""
+
+    def __init__(self, t):
+        self.t = t
+
+    def qs(self, chi: float, gamma: float):
+        n_low, n_high, floor = qs_spectrum.__defaults__
+        xi = np.concatenate([np.geomspace(floor, 0.5, n_low), 1.0 - np.geomspace(0.5, 1e-12, n_high)[1:]])
+        cdf = np.minimum(self.t.qs_table_cdf_array(chi, xi), 1.0)
+        cdf = np.maximum.accumulate(cdf)
+        return xi, cdf, float(self.t.rates(0, np.array([chi]), np.array([gamma]))[0])
+
+    def bw(self, chig: float, g: float):
+        n_half, floor = bw_spectrum.__defaults__
+        lo = np.geomspace(floor, 0.5, n_half)
+        c = self.t.bw_table_cdf_array(chig, lo)
+        xi = np.concatenate([lo, 1.0 - lo[-2::-1]])
+        cdf = np.concatenate([c, 1.0 - c[-2::-1]])
+        return xi, cdf, float(self.t.rates(1, np.array([chig]), np.array([g]))[0])
+
+
+# ----------------------------------------------------------------------------
 # the generator
 # ----------------------------------------------------------------------------
-def build_generator(chi_lepton, chi_photon, leptons: LogBins, photons: LogBins):
+def build_generator(chi_lepton, chi_photon, leptons: LogBins, photons: LogBins, model=None):
     """A for the state [primary leptons (n+1), photons (m+1), secondary leptons
     (n+1)], the +1 being each population's underflow bin (absorbing).
-    chi_lepton(gamma), chi_photon(g): the fields' chi as a function of energy."""
+    chi_lepton(gamma), chi_photon(g): the fields' chi as a function of energy;
+    model: ExactModel() (default) or TableModel(tables)."""
+    model = model or ExactModel()
     n, m = leptons.n, photons.n
     P0, G0, S0 = 0, n + 1, n + 1 + m + 1
     N = S0 + n + 1
@@ -146,15 +187,19 @@ def build_generator(chi_lepton, chi_photon, leptons: LogBins, photons: LogBins):
         chi = chi_lepton(gamma)
         if not chi > 0.0:
             continue
-        xi, cdf, G = qs_spectrum(chi)
-        W = (2.0 / 3.0) * ALPHA_F * G / gamma
+        xi, cdf, W = model.qs(chi, gamma)
+        if not W > 0.0:
+            continue
         xm, dm = _mid(xi), _masses(cdf)
-        # lead mass (below the first grid point, the xi^(1/3) tail): no visible change
-        lead = cdf[0]
+        # below the first grid point (the xi^(1/3) tail): no visible change;
+        # above the last (xi -> 1): the lepton keeps nothing, the photon all
+        lead, top = cdf[0], 1.0 - cdf[-1]
         lep = leptons.share(math.log(K) + np.log1p(-xm), dm)
         lep[j] += lead
+        lep[n] += top
         pho = photons.share(math.log(K) + np.log(xm), dm)
         pho[m] += lead
+        pho += photons.share(np.array([math.log(K)]), np.array([top]))
         for base in (P0, S0):
             col = base + j
             A[base:base + n + 1, col] += W * lep
@@ -167,13 +212,13 @@ def build_generator(chi_lepton, chi_photon, leptons: LogBins, photons: LogBins):
         chig = chi_photon(g)
         if not chig > 0.0:
             continue
-        xi, cdf, T = bw_spectrum(chig)
-        if T == 0.0:
+        xi, cdf, W = model.bw(chig, g)
+        if not W > 0.0:
             continue
-        W = ALPHA_F * chig * T / g
         xm, dm = _mid(xi), _masses(cdf)
         lep = leptons.share(math.log(g - 2.0) + np.log(xm), dm)
-        lep[n] += cdf[0] + (1.0 - cdf[-1])
+        lep[n] += cdf[0]
+        lep += leptons.share(np.array([math.log(g - 2.0)]), np.array([1.0 - cdf[-1]]))
         col = G0 + k
         A[col, col] -= W
         A[S0:S0 + n + 1, col] += 2.0 * W * lep
@@ -187,7 +232,7 @@ def solve(A: np.ndarray, f0: np.ndarray, t: float) -> np.ndarray:
 
 
 def spectra(chi_lepton, chi_photon, gamma0: float, t: float, n_lepton: int = 500, n_photon: int = 500,
-            lepton_floor: float = 1e-2, photon_floor: float = 1e-3):
+            lepton_floor: float = 1e-2, photon_floor: float = 1e-3, model=None):
     """Energy distributions at time t of one primary lepton started at gamma0,
     of the photons it and its descendants made (alive, i.e. not decayed), and
     of the secondary leptons; per primary.  Returns a dict of bin centres,
@@ -195,7 +240,7 @@ def spectra(chi_lepton, chi_photon, gamma0: float, t: float, n_lepton: int = 500
     last entry of each density being its underflow bin."""
     lep = LogBins(gamma0 - 1.0, lepton_floor, n_lepton)
     pho = LogBins(gamma0 - 1.0, photon_floor, n_photon)
-    A = build_generator(chi_lepton, chi_photon, lep, pho)
+    A = build_generator(chi_lepton, chi_photon, lep, pho, model)
     f0 = np.zeros(A.shape[0])
     f0[n_lepton - 1] = 1.0  # the top lepton bin's centre is gamma0 - 1
     f = solve(A, f0, t)

@@ -404,3 +404,14 @@ double oracle_bw_table_cdf(const oracle_tables *t, double chig, double xi)
     double p1 = a[m + 1] + (lc - l0) * (b[m + 1] - a[m + 1]) / (l1 - l0);
     return p0 + (xi - x0) * (p1 - p0) / (x1 - x0);
 }
+
+/* the forward maps above at n points (the kinetic-equation reference of the tabulated method) */
+void oracle_qs_table_cdf_array(const oracle_tables *t, double chi, int64_t n, const double *xi, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_qs_table_cdf(t, chi, xi[i]);
+}
+
+void oracle_bw_table_cdf_array(const oracle_tables *t, double chig, int64_t n, const double *xi, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_bw_table_cdf(t, chig, xi[i]);
+}

@@ -1,7 +1,9 @@
 """Writes tests/golden/ridgers_kinetic.json: the kinetic-equation spectra
 (oracle/kinetic.py) of the three test cases of Ridgers et al. (2014) that §5
-of the paper reproduces, coarse-grained to 50 log bins per population.  Calls
-only the oracle; run from the repository root:
+of the paper reproduces, coarse-grained to 50 log bins per population, for the
+exact rates and spectra ("exact") and for what the method samples with the
+paper's 256 / 256x256 tables ("tables_256", the oracle's tables).  Calls only
+the oracle; run from the repository root:
 
     python tests/golden/make_ridgers_reference.py
 
@@ -24,6 +26,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import numpy as np  # noqa: E402
 
+import oracle  # noqa: E402
 from oracle import kinetic  # noqa: E402
 
 T_C = 1.28808866712e-21  # hbar / (m_e c^2) in s (CODATA 2018)
@@ -55,17 +58,19 @@ def main():
            "units": "lepton bins: kinetic energy gamma - 1; photon bins: energy; densities per primary electron; "
                     "last entry of each density: everything below the lowest edge",
            "fine_bins": FINE, "group": GROUP, "cases": {}}
+    models = {"exact": kinetic.ExactModel(), "tables_256": kinetic.TableModel(oracle.tables())}
     for case, (g0, fs) in CASES.items():
         chi_l, chi_g = chi_functions(case)
         t = fs * 1e-15 / T_C
-        r = kinetic.spectra(chi_l, chi_g, g0, t, n_lepton=FINE, n_photon=FINE)
-        out["cases"][str(case)] = {
-            "gamma0": g0, "fs": fs, "t": t,
-            "lepton_edges": [float(v) for v in r["lepton_edges"][::GROUP]],
-            "photon_edges": [float(v) for v in r["photon_edges"][::GROUP]],
-            "primary": coarse(r["primary"]), "photons": coarse(r["photons"]), "secondary": coarse(r["secondary"]),
-            "mean_gamma_primary": float(np.sum(r["primary"][:FINE] * (1.0 + r["lepton_centres"]))),
-        }
+        entry = {"gamma0": g0, "fs": fs, "t": t}
+        for name, model in models.items():
+            r = kinetic.spectra(chi_l, chi_g, g0, t, n_lepton=FINE, n_photon=FINE, model=model)
+            entry["lepton_edges"] = [float(v) for v in r["lepton_edges"][::GROUP]]
+            entry["photon_edges"] = [float(v) for v in r["photon_edges"][::GROUP]]
+            entry[name] = {"primary": coarse(r["primary"]), "photons": coarse(r["photons"]),
+                           "secondary": coarse(r["secondary"]),
+                           "mean_gamma_primary": float(np.sum(r["primary"][:FINE] * (1.0 + r["lepton_centres"])))}
+        out["cases"][str(case)] = entry
         print(case, "done", flush=True)
     with open(os.path.join(HERE, "ridgers_kinetic.json"), "w") as f:
         json.dump(out, f, indent=1)
