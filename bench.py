@@ -73,7 +73,7 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "physics.cuh", "common.cuh", "pipeline.cuh")
+KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "evolve_core.cuh", "physics.cuh", "common.cuh", "pipeline.cuh")
 
 
 def kernel_hash() -> str:
@@ -195,11 +195,11 @@ def counts(bufs):
     return sum(int(bufs[k].count.item()) for k in ("electrons", "positrons", "photons"))
 
 
-def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None, shape=(0, 0, 0, 0)):
+def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=True, mlp=None, shape=(0, 0, 0)):
     import torch
     stats = api.Stats()
     call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats,
-                           mlp=mlp, pipeline=shape[0], threads=shape[1], ctas_per_sm=shape[2], prefetch=shape[3])
+                           mlp=mlp, pipeline=shape[0], threads=shape[1], ctas_per_sm=shape[2])
     for s in range(warmup):
         call(step0 + s)
     torch.cuda.synchronize()
@@ -404,15 +404,11 @@ def gpu_main(args):
 
     # the evolution kernel's variants on the same workload (include/qed.h, QED_EVOLVE_*)
     variants = {}
-    for name, shape in (("direct_loads", (api.QED_EVOLVE_DIRECT, 0, 0, 0)),
-                        ("direct_loads_4cta", (api.QED_EVOLVE_DIRECT, 0, 4, 0)),
-                        ("direct_l2_prefetch_1", (api.QED_EVOLVE_DIRECT, 0, 0, 1)),
-                        ("direct_l2_prefetch_2", (api.QED_EVOLVE_DIRECT, 0, 0, 2)),
-                        ("direct_l2_prefetch_4", (api.QED_EVOLVE_DIRECT, 0, 0, 4)),
-                        ("direct_4cta_l2_prefetch_1", (api.QED_EVOLVE_DIRECT, 0, 4, 1)),
-                        ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0, 0)),
-                        ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0, 0)),
-                        ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2, 0))):
+    for name, shape in (("direct_loads_4cta", (api.QED_EVOLVE_DIRECT, 0, 4)),
+                        ("direct_loads_3cta", (api.QED_EVOLVE_DIRECT, 0, 3)),
+                        ("bulk_8w_4stages", (api.QED_EVOLVE_BULK, 0, 0)),
+                        ("bulk_16w_2stages", (api.QED_EVOLVE_BULK, 512, 0)),
+                        ("bulk_8w_2stages_2cta", (api.QED_EVOLVE_BULK, 0, 2))):
         rv = time_substep(api, tabs, bufs, fire, 6, 2, ws, step0=500, shape=shape)
         evm = sum(rv["evolve_ms"]) / len(rv["evolve_ms"])
         variants[name] = {"evolve_ms": round(evm, 4), "hbm_gbs": round(BYTES_F32 * rv["n_before"] / (evm * 1e-3) / 1e9, 1),
@@ -454,11 +450,17 @@ def gpu_main(args):
         torch.cuda.empty_cache()
         from paper_2110_00256_gb300 import cascade
         c = cascade.run(tabs, steps=args.cascade_steps, scale=args.cascade_scale)
+        torch.cuda.empty_cache()
+        cs = cascade.run(tabs, steps=args.cascade_steps, scale=args.cascade_scale, fused=False)
         result["cascade"] = {"value": c["value"], "unit": UNIT, "steps": c["steps"], "patches": c["patches"],
                              "electrons_start": c["electrons"], "particles_end": c["n_end"],
                              "ms": round(c["ms"], 3), "launches_per_step": c["launches_per_step"],
                              "graph": "all steps in one CUDA graph, step counter on the device",
-                             "tuned_evolve": c["tuned"], "events": c["stats"],
+                             "push": "fused into the evolution (qed_push_substep_batched)",
+                             "separate_push": {"value": cs["value"], "ms": round(cs["ms"], 3),
+                                               "launches_per_step": cs["launches_per_step"],
+                                               "tuned_evolve": cs["tuned"]},
+                             "events": c["stats"],
                              "workload": "64 patches, counts round(10^(3+4U)) x %g (seed 7), e- beam gamma 2000 +-5%% "
                                          "vs a0=100 linear plane wave (0.8 um), dt = T_L/200, photons < 2 m_e c^2 "
                                          "discarded" % args.cascade_scale}

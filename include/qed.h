@@ -133,8 +133,6 @@ typedef struct {
                                 nor emit (the cut-off a PIC code applies to photon emission,
                                 §5); 0 = off                                                  */
     double bw_chi_cut;       /* the same for photons and pair production; 0 = off           */
-    int32_t evolve_prefetch; /* DIRECT evolution of qed_substep: each CTA asks L2 for the tile
-                                it will read this many rounds ahead (0 = none, up to 8)      */
 } qed_substep_opts;
 
 /* How qed_substep's evolution reads the particle arrays.  DIRECT: every thread
@@ -143,10 +141,10 @@ typedef struct {
  * tiles of every array into shared-memory stages with the bulk-copy engine,
  * consumer warps evaluate them; evolve_threads 512 (16 consumer warps, 2
  * stages) or evolve_ctas_per_sm 2 (8 warps, 2 stages) pick other shapes than
- * the default (8 consumer warps, 4 stages, 1 CTA per SM).  DIRECT with
- * evolve_ctas_per_sm 4 limits the kernel to 64 registers for 4 CTAs per SM
- * (otherwise 3).  All give identical results.  DEFAULT is DIRECT with 3 CTAs
- * per SM, the fastest on GB300. */
+ * the default (8 consumer warps, 4 stages, 1 CTA per SM).  DIRECT in FP32
+ * runs 4 CTAs of 256 threads per SM (64 registers), or 3 (80 registers) with
+ * evolve_ctas_per_sm 3.  All give identical results.  DEFAULT is DIRECT with 4
+ * CTAs per SM, the fastest on GB300. */
 enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 
 /* ------------------------------------------------------------------------- */
@@ -309,6 +307,17 @@ qed_status qed_push_plane_wave(const qed_species *sp, double charge, const qed_p
  * t0 + step * dt, the step read from d_step when it is not NULL. */
 qed_status qed_push_batched(const qed_batch *b, const qed_plane_wave *wave, double t0, double dt,
                             int64_t step, const int64_t *d_step, void *stream);
+/* qed_push_batched followed by qed_substep_batched, with the push fused into
+ * the evolution: one pass per particle computes the wave's fields at x (time
+ * t0 + step * dt, the step read from opts->d_step when set), pushes, and
+ * evolves the optical depth on the same registers, so that positions, momenta
+ * and optical depths cross HBM once per step.  The particles end bit for bit as
+ * with the two separate calls; the species' E and B arrays are written only if
+ * store_fields != 0 (products then inherit stale fields, which the next step's
+ * push replaces before any use).  Graph-capturable. */
+qed_status qed_push_substep_batched(const qed_tables *t, const qed_batch *b, const qed_plane_wave *wave,
+                                    double t0, double dt, uint64_t seed, int64_t step,
+                                    const qed_substep_opts *opts, int32_t store_fields, void *stream);
 /* One step of dt for every particle of `sp` (positions required) in the fields
  * already stored in its E and B arrays (uniform static fields, or fields a PIC
  * code gathered at the particles): Boris push for charge -1 or +1, straight

@@ -65,8 +65,7 @@ class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
                 ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
                 ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32),
-                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double),
-                ("evolve_prefetch", C.c_int32)]
+                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double)]
 
 
 _P = C.c_void_p
@@ -101,6 +100,8 @@ SIGNATURES = {
     "qed_tune_evolve": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float), _P]),
     "qed_push_plane_wave": (_S, [C.POINTER(Species), _D, C.POINTER(PlaneWave), _D, _D, _S, _P]),
     "qed_push_stored_fields": (_S, [C.POINTER(Species), _D, _D, _S, _P]),
+    "qed_push_substep_batched": (_S, [_P, _P, C.POINTER(PlaneWave), _D, _D, _U64, _I64, C.POINTER(SubstepOpts), _S,
+                                      _P]),
     "qed_push_batched": (_S, [_P, C.POINTER(PlaneWave), _D, _D, _I64, _P, _P]),
     "qed_mlp_create": (_S, [_P, _U64, C.POINTER(_P), _P]),
     "qed_mlp_destroy": (_S, [_P]),

@@ -23,7 +23,7 @@ __all__ = [
     "qed_tables_copy_to_host", "qed_tables_save", "qed_tables_load", "qed_init_optical_depth",
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
-    "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields",
+    "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields", "qed_push_substep_batched",
     "qed_push_batched",
 ]
 
@@ -240,7 +240,7 @@ class SubstepCall:
     def __init__(self, t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
                  photons: SpeciesBuffers, fire: list, dt: float, seed: int, photon_threshold=0.0,
                  stats: Stats | None = None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0,
-                 ctas_per_sm: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0, prefetch: int = 0):
+                 ctas_per_sm: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
         self.t = t
         self.keep = (electrons, positrons, photons, fire, stats, mlp)
         self.e, self.p, self.g = electrons.struct(), positrons.struct(), photons.struct()
@@ -252,7 +252,6 @@ class SubstepCall:
         self.opts.evolve_pipeline = int(pipeline)
         self.opts.evolve_threads = int(threads)
         self.opts.evolve_ctas_per_sm = int(ctas_per_sm)
-        self.opts.evolve_prefetch = int(prefetch)
         self.dt = float(dt)
         self.seed = int(seed)
         self.prec = electrons.prec
@@ -266,12 +265,12 @@ class SubstepCall:
 def qed_substep(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers, photons: SpeciesBuffers,
                 dt: float, seed: int, step: int, fire: list, photon_threshold=0.0, stats: Stats | None = None,
                 stream=None, mlp: "Mlp | None" = None, pipeline: int = 0, threads: int = 0, ctas_per_sm: int = 0,
-                qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0, prefetch: int = 0):
-    """One substep (include/qed.h).  pipeline / threads / ctas_per_sm / prefetch
-    choose the evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library
-    default); qs_chi_cut / bw_chi_cut are the processes' chi cut-offs (0 = off)."""
+                qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0):
+    """One substep (include/qed.h).  pipeline / threads / ctas_per_sm choose the
+    evolution kernel's variant and shape (QED_EVOLVE_*; 0 = library default);
+    qs_chi_cut / bw_chi_cut are the processes' chi cut-offs (0 = off)."""
     SubstepCall(t, electrons, positrons, photons, fire, dt, seed, photon_threshold, stats, mlp, pipeline, threads,
-                ctas_per_sm, qs_chi_cut, bw_chi_cut, prefetch)(step, stream)
+                ctas_per_sm, qs_chi_cut, bw_chi_cut)(step, stream)
 
 
 def qed_substep_noalloc(t: Tables, electrons: SpeciesBuffers, positrons: SpeciesBuffers,
@@ -391,6 +390,14 @@ def qed_substep_batched(t: Tables, b: Batch, dt: float, seed: int, step: int, op
                         stream=None):
     check(lib().qed_substep_batched(t.handle, b.handle, float(dt), int(seed), int(step),
                                     C.byref(opts) if opts is not None else None, _stream(stream)))
+
+
+def qed_push_substep_batched(t: Tables, b: Batch, wave, t0: float, dt: float, seed: int, step: int,
+                             opts: SubstepOpts | None = None, store_fields: bool = False, stream=None):
+    """Push in `wave` fused with the batched substep (include/qed.h)."""
+    check(lib().qed_push_substep_batched(t.handle, b.handle, C.byref(wave), float(t0), float(dt), int(seed), int(step),
+                                         C.byref(opts) if opts is not None else None, 1 if store_fields else 0,
+                                         _stream(stream)))
 
 
 def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:

@@ -2,7 +2,10 @@
 counter-propagating a linearly polarised plane wave whose fields are evaluated
 analytically at each particle, the substep (photon emission, pair production)
 after every push, all steps captured in one CUDA graph with a device step
-counter, and the evolution launch shape chosen by qed_tune_evolve.
+counter.  By default the push is fused into the evolution
+(qed_push_substep_batched: one pass per particle, 5 launches per step);
+fused=False runs the separate push and substep (6 launches per step) with the
+evolution launch shape chosen by qed_tune_evolve.
 
 Parameters: 64 patches with round(10^(3 + 4U)) electrons each (seed 7), gamma =
 2000 (1 + 0.05 (2U - 1)) along +x, positions uniform over one wavelength;
@@ -55,27 +58,33 @@ def make_patches(scale: float = 1.0, photon_factor: float = 40.0, prec: int = ap
 
 
 def run(tables: api.Tables, steps: int = 2000, scale: float = 1.0, photon_factor: float = 40.0,
-        prec: int = api.QED_F32, tune: bool = True, photon_threshold: float = 2.0) -> dict:
+        prec: int = api.QED_F32, tune: bool = True, photon_threshold: float = 2.0, fused: bool = True) -> dict:
     patches, counts = make_patches(scale, photon_factor, prec)
     b = api.Batch(patches, prec)
-    tuned = api.qed_tune_evolve(tables, b) if tune else None
+    tuned = api.qed_tune_evolve(tables, b) if tune and not fused else None
     wave = api.plane_wave(A0 * OMEGA_08UM, OMEGA_08UM)
     dt = 2 * math.pi / OMEGA_08UM / 200
     d_step = torch.zeros(1, dtype=torch.int64, device="cuda")
     stats = api.Stats()
     opts = api.make_opts(photon_threshold=photon_threshold, stats=stats, d_step=d_step)
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):  # first calls outside the capture
-        api.qed_push_batched(b, wave, 0.0, 0.0, 0, stream=stream)
-        api.qed_substep_batched(tables, b, 0.0, 1, 0, api.make_opts(), stream=stream)
+    with torch.cuda.stream(stream):  # first calls outside the capture (dt = 0: nothing moves or fires)
+        if fused:
+            api.qed_push_substep_batched(tables, b, wave, 0.0, 0.0, 1, 0, api.make_opts(), stream=stream)
+        else:
+            api.qed_push_batched(b, wave, 0.0, 0.0, 0, stream=stream)
+            api.qed_substep_batched(tables, b, 0.0, 1, 0, api.make_opts(), stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
         with torch.cuda.graph(graph, stream=stream):
             for _ in range(steps):
-                api.qed_push_batched(b, wave, 0.0, dt, 0, d_step, stream=stream)
-                api.qed_substep_batched(tables, b, dt, 1, 0, opts, stream=stream)
+                if fused:
+                    api.qed_push_substep_batched(tables, b, wave, 0.0, dt, 1, 0, opts, stream=stream)
+                else:
+                    api.qed_push_batched(b, wave, 0.0, dt, 0, d_step, stream=stream)
+                    api.qed_substep_batched(tables, b, dt, 1, 0, opts, stream=stream)
     capture_s = time.perf_counter() - t0
 
     def live():
@@ -100,5 +109,5 @@ def run(tables: api.Tables, steps: int = 2000, scale: float = 1.0, photon_factor
     particle_steps = n0 * steps + appended * steps / 2.0
     return {"patches": int(len(counts)), "electrons": int(counts.sum()), "steps": steps, "ms": ms,
             "particle_steps": particle_steps, "value": particle_steps / (ms * 1e-3), "n_start": n0, "n_end": n1,
-            "graph_nodes_per_step": 6, "capture_s": capture_s, "tuned": tuned, "stats": s,
-            "launches_per_step": 6}
+            "graph_nodes_per_step": 5 if fused else 6, "capture_s": capture_s, "tuned": tuned, "stats": s,
+            "launches_per_step": 5 if fused else 6, "fused": fused}

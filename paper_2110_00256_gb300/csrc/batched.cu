@@ -39,6 +39,7 @@ struct qed_batch {
     qed::ClampEntry *d_clamp;  // [6 n] species and firing counts to clamp
     void *d_push;      // PushSeg<T>[3 n] when every species has positions, else NULL
     bool vec;
+    bool push_vec;     // vec, and the positions 16-byte aligned too
     int64_t capacity_sum, fire_capacity_max;
     int threads, ctas_per_sm;  // tuned evolution launch shape (0: default)
 };
@@ -201,13 +202,15 @@ static qed_status build_batch(const qed_patch *patches, int n, qed_batch *b, cud
         g.fire_idx = p.fire[2].idx, g.fire_chi = p.fire[2].chi, g.fire_count = p.fire[2].d_count;
         g.fire_cap = p.fire[2].capacity;
     }
-    bool positions = true;
+    bool positions = true, pos_al16 = true;
     std::vector<PushSeg<T>> push(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
         const qed_species *sp[3] = {&patches[i].electrons, &patches[i].positrons, &patches[i].photons};
         const double q[3] = {-1.0, 1.0, 0.0};
         for (int k = 0; k < 3; ++k) {
             positions = positions && sp[k]->x && sp[k]->y && sp[k]->z;
+            for (const void *a : {sp[k]->x, sp[k]->y, sp[k]->z})
+                pos_al16 = pos_al16 && ((uintptr_t)a & 15u) == 0;
             push[3 * i + k] = push_seg<T>(sp[k], q[k]);
         }
     }
@@ -231,14 +234,18 @@ static qed_status build_batch(const qed_patch *patches, int n, qed_batch *b, cud
     }
     QED_CUDA_TRY(cudaStreamSynchronize(st));
     b->vec = vec;
+    b->push_vec = vec && positions && pos_al16;
     b->capacity_sum = capsum;
     b->fire_capacity_max = fmax;
     return QED_OK;
 }
 
+// wave != NULL: the push in that wave is fused into the evolution (one pass
+// per particle), at time t0 + step * dt (step from opts->d_step when set)
 template <typename T>
 static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, double dt, uint64_t seed, int64_t step,
-                                       const qed_substep_opts *o, cudaStream_t st)
+                                       const qed_substep_opts *o, cudaStream_t st, const qed_plane_wave *wave = nullptr,
+                                       double t0 = 0.0, int store_fields = 0)
 {
     const int n = b->n_patches;
     zero_counts_kernel<<<(3 * n + 255) / 256, 256, 0, st>>>(b->d_zero, 3 * n);
@@ -246,9 +253,13 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
     const int threads = (o && o->evolve_threads) ? o->evolve_threads : (b->threads ? b->threads : 256);
     const int ctas = (o && o->evolve_ctas_per_sm) ? o->evolve_ctas_per_sm : b->ctas_per_sm;
     if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
-    qed_status s = launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
-                                             o ? (T)o->qs_chi_cut : T(0), o ? (T)o->bw_chi_cut : T(0),
-                                             o ? (long long *)o->d_stats : nullptr, 0, b->vec, threads, ctas, st);
+    const T cut_qs = o ? (T)o->qs_chi_cut : T(0), cut_bw = o ? (T)o->bw_chi_cut : T(0);
+    long long *stats = o ? (long long *)o->d_stats : nullptr;
+    qed_status s = wave ? launch_push_evolve<T>((const EvolveSeg<T> *)b->d_evolve, b->d_push, 3 * n, make_view<T>(t),
+                                                wave_params(wave), t0, dt, o ? o->d_step : nullptr, step, cut_qs,
+                                                cut_bw, stats, store_fields, b->push_vec, st)
+                        : launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
+                                                    cut_qs, cut_bw, stats, 0, b->vec, threads, ctas, st);
     if (s) return s;
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
     const bool mlp = o && o->sampler == 1;
@@ -327,6 +338,25 @@ extern "C" qed_status qed_substep_batched(const qed_tables *t, const qed_batch *
     cudaStream_t st = as_stream(stream);
     return b->prec == QED_F32 ? substep_batched_impl<float>(t, b, dt, seed, step, opts, st)
                               : substep_batched_impl<double>(t, b, dt, seed, step, opts, st);
+}
+
+extern "C" qed_status qed_push_substep_batched(const qed_tables *t, const qed_batch *b, const qed_plane_wave *wave,
+                                               double t0, double dt, uint64_t seed, int64_t step,
+                                               const qed_substep_opts *opts, int32_t store_fields, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if ((s = check_tables(t))) return s;
+    if (!b) QED_FAIL(QED_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->d_push) QED_FAIL(QED_ERR_INVALID_ARG, "the batch's species have no positions");
+    if ((s = check_wave(wave))) return s;
+    if ((s = check_opts(opts))) return s;
+    if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    if (!std::isfinite(t0)) QED_FAIL(QED_ERR_INVALID_ARG, "t0 must be finite");
+    cudaStream_t st = as_stream(stream);
+    return b->prec == QED_F32
+               ? substep_batched_impl<float>(t, b, dt, seed, step, opts, st, wave, t0, store_fields != 0)
+               : substep_batched_impl<double>(t, b, dt, seed, step, opts, st, wave, t0, store_fields != 0);
 }
 
 extern "C" qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t *threads_out,

@@ -185,8 +185,6 @@ qed_status check_opts(const qed_substep_opts *o)
     if (o && !(o->photon_threshold >= 0.0)) QED_FAIL(QED_ERR_INVALID_ARG, "photon_threshold must be >= 0");
     if (o && !(o->qs_chi_cut >= 0.0 && o->bw_chi_cut >= 0.0))
         QED_FAIL(QED_ERR_INVALID_ARG, "qs_chi_cut and bw_chi_cut must be >= 0");
-    if (o && (o->evolve_prefetch < 0 || o->evolve_prefetch > 8))
-        QED_FAIL(QED_ERR_INVALID_ARG, "evolve_prefetch must be in [0, 8]");
     if (o && (o->evolve_pipeline < QED_EVOLVE_DEFAULT || o->evolve_pipeline > QED_EVOLVE_BULK))
         QED_FAIL(QED_ERR_INVALID_ARG, "unknown evolve_pipeline %d", o->evolve_pipeline);
     return QED_OK;
@@ -205,7 +203,6 @@ static qed_status substep_impl(const qed_tables *t, const qed_species *e, const 
     a.stats = o ? (long long *)o->d_stats : nullptr;
     a.chi_cut[QED_PROC_QS] = o ? (T)o->qs_chi_cut : T(0);
     a.chi_cut[QED_PROC_BW] = o ? (T)o->bw_chi_cut : T(0);
-    a.prefetch = o ? o->evolve_prefetch : 0;
     bool vec = fill_seg<T>(a.seg[0], e, QED_PROC_QS, &fire[0]);
     vec = fill_seg<T>(a.seg[1], p, QED_PROC_QS, &fire[1]) && vec;
     vec = fill_seg<T>(a.seg[2], g, QED_PROC_BW, &fire[2]) && vec;

@@ -33,7 +33,6 @@ struct EvolveArgs {
     T dt;
     T chi_cut[2];  // per process (QED_PROC_QS, QED_PROC_BW): below it the rate is taken as zero
     int n_seg;
-    int prefetch;  // L2 prefetch distance in rounds of the grid over the tiles; 0 = none
 };
 
 int sm_count();

@@ -76,11 +76,4 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// asks L2 to fetch `bytes` (a multiple of 16; 16-byte-aligned address) of
-// global memory; no completion to wait for
-__device__ __forceinline__ void l2_prefetch_bulk(const void *p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 }  // namespace qed

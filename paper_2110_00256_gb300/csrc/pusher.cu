@@ -16,28 +16,6 @@ namespace qed {
 
 int sm_count();
 
-__device__ __forceinline__ void d_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
-__device__ __forceinline__ void d_sincos(double x, double *s, double *c) { sincos(x, s, c); }
-
-// phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E.
-// Evaluated in the working precision (over the cascade's 10 periods the FP32
-// phase keeps ~1e-5 rad).
-template <typename T>
-__device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, T &ex, T &ey, T &ez, T &bx, T &by,
-                                            T &bz)
-{
-    const T d = (T)w.direction;
-    const T phi = (T)w.omega * ((T)t - d * x) + (T)w.phase0;
-    T s, c;
-    d_sincos(phi, &s, &c);
-    ex = T(0);
-    ey = (T)w.e0 * c;
-    ez = w.circular ? (T)w.e0 * s : T(0);
-    bx = T(0);
-    by = -d * ez;
-    bz = d * ey;
-}
-
 // momentum (Boris) and position update of particle i with the fields (ex .. bz)
 template <typename T>
 __device__ __forceinline__ void advance(const PushSeg<T> &g, int64_t i, T x, T ex, T ey, T ez, T bx, T by, T bz,
@@ -45,25 +23,8 @@ __device__ __forceinline__ void advance(const PushSeg<T> &g, int64_t i, T x, T e
 {
     T px = g.px[i], py = g.py[i], pz = g.pz[i];
     T vx, vy, vz;
-    if (g.q == T(0)) {
-        const T pm = sqrt(px * px + py * py + pz * pz);
-        const T inv = pm > T(0) ? T(1) / pm : T(0);
-        vx = px * inv, vy = py * inv, vz = pz * inv;
-    } else {
-        const T h = T(0.5) * g.q * dt;
-        const T mx = px + h * ex, my = py + h * ey, mz = pz + h * ez;  // half electric kick
-        const T gm = sqrt(T(1) + mx * mx + my * my + mz * mz);
-        const T tx = h * bx / gm, ty = h * by / gm, tz = h * bz / gm;
-        const T f = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
-        const T sx = f * tx, sy = f * ty, sz = f * tz;
-        const T qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
-        px = mx + (qy * sz - qz * sy) + h * ex;
-        py = my + (qz * sx - qx * sz) + h * ey;
-        pz = mz + (qx * sy - qy * sx) + h * ez;
-        const T ig = T(1) / sqrt(T(1) + px * px + py * py + pz * pz);
-        vx = px * ig, vy = py * ig, vz = pz * ig;
-        g.px[i] = px, g.py[i] = py, g.pz[i] = pz;
-    }
+    boris_move<T>(g.q, dt, ex, ey, ez, bx, by, bz, px, py, pz, vx, vy, vz);
+    if (g.q != T(0)) g.px[i] = px, g.py[i] = py, g.pz[i] = pz;
     g.x[i] = x + vx * dt;
     g.y[i] = g.y[i] + vy * dt;
     g.z[i] = g.z[i] + vz * dt;

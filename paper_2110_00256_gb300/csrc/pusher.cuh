@@ -1,7 +1,9 @@
-// pusher.cuh -- descriptors of the plane-wave particle push (see pusher.cu).
+// pusher.cuh -- descriptors and per-particle arithmetic of the particle push
+// (see pusher.cu); the fused push + evolution uses the same functions.
 #pragma once
 
 #include "common.cuh"
+#include "evolve.cuh"
 
 namespace qed {
 
@@ -18,12 +20,68 @@ struct PushSeg {
     T q;
 };
 
+__device__ __forceinline__ void d_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void d_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+
+// phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E.
+// Evaluated in the working precision (over the cascade's 10 periods the FP32
+// phase keeps ~1e-5 rad).
+template <typename T>
+__device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, T &ex, T &ey, T &ez, T &bx, T &by,
+                                            T &bz)
+{
+    const T d = (T)w.direction;
+    const T phi = (T)w.omega * ((T)t - d * x) + (T)w.phase0;
+    T s, c;
+    d_sincos(phi, &s, &c);
+    ex = T(0);
+    ey = (T)w.e0 * c;
+    ez = w.circular ? (T)w.e0 * s : T(0);
+    bx = T(0);
+    by = -d * ez;
+    bz = d * ey;
+}
+
+// one step of the momentum of a particle of charge q (relativistic Boris
+// rotation; q = 0: a photon, unchanged) and the velocity it then moves with
+template <typename T>
+__device__ __forceinline__ void boris_move(T q, T dt, T ex, T ey, T ez, T bx, T by, T bz, T &px, T &py, T &pz,
+                                           T &vx, T &vy, T &vz)
+{
+    if (q == T(0)) {
+        const T pm = sqrt(px * px + py * py + pz * pz);
+        const T inv = pm > T(0) ? T(1) / pm : T(0);
+        vx = px * inv, vy = py * inv, vz = pz * inv;
+        return;
+    }
+    const T h = T(0.5) * q * dt;
+    const T mx = px + h * ex, my = py + h * ey, mz = pz + h * ez;  // half electric kick
+    const T gm = sqrt(T(1) + mx * mx + my * my + mz * mz);
+    const T tx = h * bx / gm, ty = h * by / gm, tz = h * bz / gm;
+    const T f = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+    const T sx = f * tx, sy = f * ty, sz = f * tz;
+    const T qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
+    px = mx + (qy * sz - qz * sy) + h * ex;
+    py = my + (qz * sx - qx * sz) + h * ey;
+    pz = mz + (qx * sy - qy * sx) + h * ez;
+    const T ig = T(1) / sqrt(T(1) + px * px + py * py + pz * pz);
+    vx = px * ig, vy = py * ig, vz = pz * ig;
+}
+
 template <typename T>
 PushSeg<T> push_seg(const qed_species *s, double q);
 
 template <typename T>
 qed_status launch_push(const void *d_segs, int n_seg, const WaveParams &w, double t0, double dt,
                        const int64_t *d_step, int64_t step, int64_t capacity, cudaStream_t st);
+
+// the fused push + evolution over segments in device memory (fused.cu): d_push
+// holds PushSeg<T>[n_seg] in the order of d_segs; store_fields != 0 also writes
+// the fields into the species; vec: every array 16-byte aligned
+template <typename T>
+qed_status launch_push_evolve(const EvolveSeg<T> *d_segs, const void *d_push, int n_seg, const TablesView<T> &tab,
+                              const WaveParams &w, double t0, double dt, const int64_t *d_step, int64_t step,
+                              T cut_qs, T cut_bw, long long *stats, int store_fields, bool vec, cudaStream_t st);
 
 qed_status check_wave(const qed_plane_wave *w);
 WaveParams wave_params(const qed_plane_wave *w);

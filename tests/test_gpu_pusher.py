@@ -198,3 +198,57 @@ def test_push_stored_fields_fp64_matches_oracle(api, charge):
         assert np.array_equal(g[c], E[:, i]), c
     for i, c in enumerate(("bx", "by", "bz")):
         assert np.array_equal(g[c], B[:, i]), c
+
+
+def _wave_patches(api, prec, sizes, seed):
+    from paper_2110_00256_gb300 import workloads
+    out = []
+    r = np.random.default_rng(seed)
+    for i, n in enumerate(sizes):
+        d = {}
+        for j, (k, m) in enumerate((("electrons", n), ("positrons", n // 3), ("photons", n))):
+            h = workloads.paper_benchmark(m, seed + 10 * i + j, (3 * i + j) * 10 ** 9)
+            h["tau"] *= 0.05
+            for c in ("ex", "ey", "ez", "bx", "by", "bz"):
+                h[c] = np.zeros(m)
+            h.update(x=r.uniform(0, 2 * math.pi / OMEGA, m), y=r.uniform(-1, 1, m), z=r.uniform(-1, 1, m))
+            b = api.SpeciesBuffers(3 * m + 64, prec, positions=True)
+            if m:
+                b.set(h)
+            d[k] = b
+        d["fire"] = [api.FireBuffers(d[k].capacity) for k in ("electrons", "positrons", "photons")]
+        out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("store_fields", [False, True])
+@pytest.mark.parametrize("prec_name", ["f32", "f64"])
+def test_fused_push_substep_equals_separate(api, prec_name, store_fields):
+    """qed_push_substep_batched (push fused into the evolution) against
+    qed_push_batched + qed_substep_batched, 30 steps of a circularly polarised
+    a0 = 100 wave on patches of uneven size: every particle ends with the same
+    bits (the fields too when the fused call stores them)."""
+    prec = api.QED_F32 if prec_name == "f32" else api.QED_F64
+    tabs = api.qed_tables_generate(api.table_params(qs_n_chi=128, qs_n_xi=128, bw_n_chi=128, bw_n_xi=128))
+    sizes = [1, 700, 5003, 0, 20000, 33]
+    sep, fus = _wave_patches(api, prec, sizes, 4), _wave_patches(api, prec, sizes, 4)
+    bs, bf = api.Batch(sep, prec), api.Batch(fus, prec)
+    w = api.plane_wave(E0, OMEGA, 0.2, True)
+    ss, sf = api.Stats(), api.Stats()
+    for k in range(30):
+        api.qed_push_batched(bs, w, 3.0, DT, k)
+        api.qed_substep_batched(tabs, bs, DT, 17, k, api.make_opts(stats=ss))
+        api.qed_push_substep_batched(tabs, bf, w, 3.0, DT, 17, k, api.make_opts(stats=sf), store_fields=store_fields)
+    torch.cuda.synchronize()
+    assert ss.as_dict() == sf.as_dict()
+    assert sf.as_dict()["qs_events"] > 1000 and sf.as_dict()["dropped_capacity"] == 0
+    cols = ("px", "py", "pz", "x", "y", "z", "tau", "tau_c", "weight", "id")
+    if store_fields:
+        cols += ("ex", "ey", "ez", "bx", "by", "bz")
+    for a, b in zip(sep, fus):
+        for k in ("electrons", "positrons", "photons"):
+            ha, hb = a[k].to_host(), b[k].to_host()
+            oa, ob = np.argsort(ha["id"], kind="stable"), np.argsort(hb["id"], kind="stable")
+            for c in cols:
+                if c in ha:
+                    assert np.array_equal(ha[c][oa], hb[c][ob]), (k, c)

@@ -69,8 +69,14 @@ def test_ridgers_spectra_match_kinetic_equation(api, tables, reference, case, pr
     assert out["primary"].shape[0] == N
     w = {"primary": _check("primary", out["primary"], ref["lepton_edges"], ref["primary"], N, 1.0),
          "photons": _check("photons", out["photons"], ref["photon_edges"], ref["photons"], N, 3.0)}
-    mean = float(np.mean(1.0 + out["primary"]))
-    assert mean == pytest.approx(ref["mean_gamma_primary"], rel=5e-3)
+    # the mean primary energy within 4 standard errors plus 0.3 %: the substep
+    # fires at most once per step with probability 1 - exp(-W dt), which
+    # undercounts emissions by ~W dt / 2 (W dt < 0.6 % per step in all cases)
+    g = 1.0 + out["primary"]
+    mean, se = float(np.mean(g)), float(np.std(g)) / np.sqrt(N)
+    assert abs(mean - ref["mean_gamma_primary"]) <= 4 * se + 3e-3 * ref["mean_gamma_primary"]
+    emitted = sum(ref["photons"]) + 0.5 * sum(ref["secondary"])
+    assert st["qs_events"] / N == pytest.approx(emitted, rel=1e-2)
     if case == 3:  # pairs are only plentiful at chi = 9
         w["secondary"] = _check("secondary", out["secondary"], ref["lepton_edges"], ref["secondary"], N, 3.0)
     print(case, prec_name, w, "mean gamma", mean, ref["mean_gamma_primary"], st)

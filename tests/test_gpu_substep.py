@@ -257,24 +257,22 @@ def test_full_size_fp32_workload_sampled(api, tabs):
         assert f.sum() > 0
 
 
-@pytest.mark.parametrize("variant", [(2, 0, 0, 0), (2, 512, 0, 0), (2, 0, 2, 0), (1, 0, 4, 0), (1, 0, 0, 1),
-                                     (1, 0, 0, 3), (1, 0, 4, 2)],
-                         ids=["bulk8w4s", "bulk16w2s", "bulk8w2sx2", "direct4cta", "direct_pf1", "direct_pf3",
-                              "direct4cta_pf2"])
+@pytest.mark.parametrize("variant", [(2, 0, 0), (2, 512, 0), (2, 0, 2), (1, 0, 3)],
+                         ids=["bulk8w4s", "bulk16w2s", "bulk8w2sx2", "direct3cta"])
 def test_evolution_variants_equal_direct_loads(api, tabs, variant):
     """Every variant of the evolution kernel (bulk copies into shared memory,
-    four CTAs per SM, L2 prefetch ahead) gives the same bits as the default
-    direct loads: the same particles fire with the same chi, and every particle
+    three CTAs per SM) gives the same bits as the default direct loads (four
+    CTAs per SM): the same particles fire with the same chi, and every particle
     (secondaries included) ends identical.  Sizes give full tiles, a ragged
     tail, and a species smaller than one tile.  Every destination has room for
     every event (which events run when one fills up depends on the order of the
     firing list)."""
     _, t = tabs
-    pipe_v, threads, ctas, pf = variant
-    host = _inputs(600_003, 41, n_pos=1000)  # more tiles than the grid has CTAs (prefetch ahead)
+    pipe_v, threads, ctas = variant
+    host = _inputs(600_003, 41, n_pos=1000)  # more tiles than the grid has CTAs
     host["photons"] = _inputs(70_001, 42)["photons"]
     out = {}
-    for key, (pipe, th, ct, p) in (("ref", (api.QED_EVOLVE_DIRECT, 0, 0, 0)), ("var", (pipe_v, threads, ctas, pf))):
+    for key, (pipe, th, ct) in (("ref", (api.QED_EVOLVE_DIRECT, 0, 0)), ("var", (pipe_v, threads, ctas))):
         bufs, fire = {}, []
         for k in SPECIES:
             n = len(host[k]["px"])
@@ -284,7 +282,7 @@ def test_evolution_variants_equal_direct_loads(api, tabs, variant):
             fire.append(api.FireBuffers(b.capacity))
         stats = api.Stats()
         api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 5, 2, fire, stats=stats,
-                        pipeline=pipe, threads=th, ctas_per_sm=ct, prefetch=p)
+                        pipeline=pipe, threads=th, ctas_per_sm=ct)
         torch.cuda.synchronize()
         fl = []
         for f in fire:
