@@ -208,11 +208,12 @@ def _wave_patches(api, prec, sizes, seed):
         d = {}
         for j, (k, m) in enumerate((("electrons", n), ("positrons", n // 3), ("photons", n))):
             h = workloads.paper_benchmark(m, seed + 10 * i + j, (3 * i + j) * 10 ** 9)
-            h["tau"] *= 0.05
             for c in ("ex", "ey", "ez", "bx", "by", "bz"):
                 h[c] = np.zeros(m)
             h.update(x=r.uniform(0, 2 * math.pi / OMEGA, m), y=r.uniform(-1, 1, m), z=r.uniform(-1, 1, m))
-            b = api.SpeciesBuffers(3 * m + 64, prec, positions=True)
+            # room for every event (which events run when a destination fills up
+            # depends on the order of the firing lists)
+            b = api.SpeciesBuffers(m + 8 * n + 64, prec, positions=True)
             if m:
                 b.set(h)
             d[k] = b
@@ -225,7 +226,7 @@ def _wave_patches(api, prec, sizes, seed):
 @pytest.mark.parametrize("prec_name", ["f32", "f64"])
 def test_fused_push_substep_equals_separate(api, prec_name, store_fields):
     """qed_push_substep_batched (push fused into the evolution) against
-    qed_push_batched + qed_substep_batched, 30 steps of a circularly polarised
+    qed_push_batched + qed_substep_batched, 12 steps of a circularly polarised
     a0 = 100 wave on patches of uneven size: every particle ends with the same
     bits (the fields too when the fused call stores them)."""
     prec = api.QED_F32 if prec_name == "f32" else api.QED_F64
@@ -235,13 +236,13 @@ def test_fused_push_substep_equals_separate(api, prec_name, store_fields):
     bs, bf = api.Batch(sep, prec), api.Batch(fus, prec)
     w = api.plane_wave(E0, OMEGA, 0.2, True)
     ss, sf = api.Stats(), api.Stats()
-    for k in range(30):
+    for k in range(12):
         api.qed_push_batched(bs, w, 3.0, DT, k)
         api.qed_substep_batched(tabs, bs, DT, 17, k, api.make_opts(stats=ss))
         api.qed_push_substep_batched(tabs, bf, w, 3.0, DT, 17, k, api.make_opts(stats=sf), store_fields=store_fields)
     torch.cuda.synchronize()
-    assert ss.as_dict() == sf.as_dict()
-    assert sf.as_dict()["qs_events"] > 1000 and sf.as_dict()["dropped_capacity"] == 0
+    assert ss.as_dict()["dropped_capacity"] == 0 and sf.as_dict()["dropped_capacity"] == 0
+    assert ss.as_dict() == sf.as_dict() and sf.as_dict()["qs_events"] > 1000
     cols = ("px", "py", "pz", "x", "y", "z", "tau", "tau_c", "weight", "id")
     if store_fields:
         cols += ("ex", "ey", "ez", "bx", "by", "bz")
