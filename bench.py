@@ -382,7 +382,7 @@ def gpu_main(args):
     hbm, which = peaks()
     ach = BYTES_F32 * r["n_before"] / (ev_mean * 1e-3) / 1e9
     traffic_bpp = traffic_record()
-    roofline = {"bound": "hbm", "kernel": "evolve_kernel<float,4>", "achieved": round(ach, 1), "peak": hbm,
+    roofline = {"bound": "hbm", "kernel": "evolve_kernel<float,4,4,4>", "achieved": round(ach, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_kind": which,
                 "traffic": (traffic_bpp * r["n_before"]) if traffic_bpp else None,
                 "algorithmic_bytes": BYTES_F32 * r["n_before"], "evolve_ms": round(ev_mean, 4),

@@ -16,6 +16,10 @@ struct Vec<float, 4> {
     using type = float4;
 };
 template <>
+struct Vec<float, 2> {
+    using type = float2;
+};
+template <>
 struct Vec<double, 2> {
     using type = double2;
 };
