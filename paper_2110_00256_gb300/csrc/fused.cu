@@ -35,8 +35,10 @@ __device__ __forceinline__ void store_live(T *p, int64_t i0, int64_t n, bool ful
     }
 }
 
+// FP32: two particles per thread, 4 CTAs of 256 per SM (64 registers), the
+// fastest of VEC 1 / 2 / 4 x 2 .. 4 CTAs per SM measured on GB300
 template <typename T, int VEC, int THREADS>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
     push_evolve_kernel(const EvolveSeg<T> *__restrict__ segs, const PushSeg<T> *__restrict__ psegs, int n_seg,
                        TablesView<T> tab, WaveParams w, double t0, double dt_d, const int64_t *d_step, int64_t step,
                        T cut_qs, T cut_bw, long long *stats, int store_fields)
@@ -140,7 +142,7 @@ qed_status launch_push_evolve(const EvolveSeg<T> *d_segs, const void *d_push, in
     if (n_seg <= 0) return QED_OK;
     const PushSeg<T> *p = (const PushSeg<T> *)d_push;
     if (vec) {
-        constexpr int V = sizeof(T) == 4 ? 4 : 2;
+        constexpr int V = 2;
         return launch_fused_impl<T, V>(d_segs, p, n_seg, tab, w, t0, dt, d_step, step, cut_qs, cut_bw, stats,
                                        store_fields, st);
     }

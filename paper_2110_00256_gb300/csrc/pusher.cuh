@@ -8,7 +8,7 @@
 namespace qed {
 
 struct WaveParams {
-    double e0, omega, phase0;
+    double e0, omega_pi, phase0_pi;  // amplitude; omega / pi and phase0 / pi (phases in half-turns)
     int circular, direction;
 };
 
@@ -20,20 +20,21 @@ struct PushSeg {
     T q;
 };
 
-__device__ __forceinline__ void d_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
-__device__ __forceinline__ void d_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+// sin and cos of pi u (the argument reduction of a half-turn multiple is exact)
+__device__ __forceinline__ void d_sincospi(float u, float *s, float *c) { sincospif(u, s, c); }
+__device__ __forceinline__ void d_sincospi(double u, double *s, double *c) { sincospi(u, s, c); }
 
 // phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E.
-// Evaluated in the working precision (over the cascade's 10 periods the FP32
-// phase keeps ~1e-5 rad).
+// Evaluated in the working precision, in half-turns (over the cascade's 10
+// periods the FP32 phase keeps ~1e-5 rad).
 template <typename T>
 __device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, T &ex, T &ey, T &ez, T &bx, T &by,
                                             T &bz)
 {
     const T d = (T)w.direction;
-    const T phi = (T)w.omega * ((T)t - d * x) + (T)w.phase0;
+    const T u = (T)w.omega_pi * ((T)t - d * x) + (T)w.phase0_pi;
     T s, c;
-    d_sincos(phi, &s, &c);
+    d_sincospi(u, &s, &c);
     ex = T(0);
     ey = (T)w.e0 * c;
     ez = w.circular ? (T)w.e0 * s : T(0);
@@ -56,8 +57,8 @@ __device__ __forceinline__ void boris_move(T q, T dt, T ex, T ey, T ez, T bx, T 
     }
     const T h = T(0.5) * q * dt;
     const T mx = px + h * ex, my = py + h * ey, mz = pz + h * ez;  // half electric kick
-    const T gm = sqrt(T(1) + mx * mx + my * my + mz * mz);
-    const T tx = h * bx / gm, ty = h * by / gm, tz = h * bz / gm;
+    const T hg = h / sqrt(T(1) + mx * mx + my * my + mz * mz);
+    const T tx = hg * bx, ty = hg * by, tz = hg * bz;
     const T f = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
     const T sx = f * tx, sy = f * ty, sz = f * tz;
     const T qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
