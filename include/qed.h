@@ -109,7 +109,8 @@ enum {
     QED_STAT_WAIT_TIMEOUT = 9,       /* CTAs that gave up a bounded wait of the copy
                                         pipeline (never expected; the launch's results
                                         are then incomplete)                             */
-    QED_STAT_COUNT = 10
+    QED_STAT_SCHWINGER_PAIRS = 10,   /* pairs made by qed_schwinger_pairs                  */
+    QED_STAT_COUNT = 11
 };
 
 typedef struct {
@@ -152,6 +153,35 @@ enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 /* ------------------------------------------------------------------------- */
 const char *qed_last_error_message(void);
 const char *qed_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* units (§3.3: one normalised system inside, conversions at the boundary)    */
+/* ------------------------------------------------------------------------- */
+/* The SI value of one unit of each quantity of a unit system (CODATA 2018).
+ * Converting a value v from system a to system b: v * a.x / b.x. */
+typedef struct {
+    double length;   /* m     */
+    double time;     /* s     */
+    double momentum; /* kg m/s */
+    double energy;   /* J     */
+    double e_field;  /* V/m   */
+    double b_field;  /* T     */
+} qed_unit_scales;
+
+/* The library's own units: length hbar/(m_e c), time hbar/(m_e c^2), momentum
+ * m_e c, energy m_e c^2, E in E_s = m_e^2 c^3/(q_e hbar) (§2, the Schwinger
+ * field, ~1.32e18 V/m), B in E_s/c. */
+qed_status qed_units_library(qed_unit_scales *out);
+/* A PIC code normalised to a reference angular frequency omega_r (rad/s):
+ * length c/omega_r, time 1/omega_r, momentum m_e c, energy m_e c^2, E in
+ * m_e c omega_r/q_e, B in m_e omega_r/q_e.  Also the reference-length form with
+ * omega_r = 2 pi c / lambda_r. */
+qed_status qed_units_reference_frequency(double omega_r, qed_unit_scales *out);
+qed_status qed_units_reference_length(double lambda_r, qed_unit_scales *out);
+/* Heaviside-Lorentz natural units (hbar = c = 1) with 1 MeV as the reference
+ * energy: length hbar c/MeV, time hbar/MeV, momentum MeV/c, energy MeV, and
+ * fields in MeV^2 (q_e = sqrt(4 pi alpha)). */
+qed_status qed_units_heaviside_lorentz_mev(qed_unit_scales *out);
 
 /* ------------------------------------------------------------------------- */
 /* tables (§3.1, §3.2; generation §3 and §5)                                  */
@@ -240,6 +270,33 @@ qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        const qed_species *positrons, const qed_species *photons, double dt,
                        uint64_t seed, int64_t step, const qed_substep_opts *opts,
                        qed_precision prec, const qed_fire_list *fire, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Schwinger pair production (§2.3)                                          */
+/* ------------------------------------------------------------------------- */
+/* Cells of the field mesh: n cells, structure of arrays in the precision of the
+ * call, fields in E_s and E_s/c; cell positions (for the products) or NULL. */
+typedef struct {
+    const void *ex, *ey, *ez, *bx, *by, *bz;
+    const void *x, *y, *z;
+    int64_t n;
+} qed_cells;
+
+/* Pairs made from the vacuum in every cell during dt (Eq. (shw); normalised:
+ * rate = eps eta coth(pi eta/eps) exp(-pi/eps) / (4 pi^2) per hbar/(m_e c)
+ * cubed per hbar/(m_e c^2), eps and eta from the field invariants).  Each cell
+ * of volume dv draws a Poisson number of pairs of weight `weight` with mean
+ * rate dv dt / weight (Philox counter (cell, step, 4): inversion up to a mean
+ * of 100, the normal approximation above).  Pairs start at rest (§2.3) with
+ * the cell's fields and position, ids from Philox (cell, step, 5 + 256 j) and
+ * optical depths from their ids; they are appended to `electrons` and
+ * `positrons` (capacity-checked: a pair without room in both is not made and is
+ * counted as dropped).  Rate and mean in FP64 at either precision.  d_stats:
+ * QED_STAT_SCHWINGER_PAIRS and QED_STAT_DROPPED_CAPACITY, or NULL. */
+qed_status qed_schwinger_pairs(const qed_cells *cells, double dv, double dt, double weight, uint64_t seed,
+                               int64_t step, const qed_species *electrons,
+                               const qed_species *positrons, qed_precision prec, int64_t *d_stats,
+                               void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* many patches per launch                                                    */

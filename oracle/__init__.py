@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["quad_bessel.c", "rates_tables.c", "substep.c"]
+_SOURCES = ["quad_bessel.c", "rates_tables.c", "substep.c", "schwinger.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -91,6 +91,10 @@ def lib():
             "oracle_bw_cdf": (_D, [_D, _D]),
             "oracle_qs_cdf_sorted": (None, [_D, _I64, _P, _P]),
             "oracle_qs_S_array": (None, [_D, _I64, _P, _P]),
+            "oracle_schwinger_rate": (_D, [_D, _D, _D, _D, _D, _D]),
+            "oracle_poisson": (_I64, [_D, _U64, _U64, _I64]),
+            "oracle_schwinger_pair_ids": (None, [_U64, _U64, _I64, _I64, _P]),
+            "oracle_schwinger_cells": (None, [_I64, _P, _P, _P, _P, _P, _P, _D, _D, _D, _U64, _I64, _P, _P]),
             "oracle_bw_bracket_array": (None, [_D, _I64, _P, _P]),
             "oracle_bw_cdf_sorted": (None, [_D, _I64, _P, _P]),
             "oracle_build_qs_tables": (None, [_D, _D, C.c_int, C.c_int, _D, _P, _P]),
@@ -540,3 +544,46 @@ def substep(t: OracleTables, species: dict, dt: float, seed: int, step: int,
     result["chi"] = chis
     result["n_new"] = {k: len(v) for k, v in new.items()}
     return result
+
+
+# ----------------------------------------------------------------------------------------
+# Schwinger pair production per cell (§2.3, Eq. (shw)); see schwinger.c
+# ----------------------------------------------------------------------------------------
+def schwinger_rate(E, B) -> float:
+    """Pairs per unit volume per unit time (units 1/(lambda_C^3 t_C)) in fields E, B (units of E_s)."""
+    return lib().oracle_schwinger_rate(*map(float, (*E, *B)))
+
+
+def poisson(lam: float, seed: int, cell: int, step: int) -> int:
+    return int(lib().oracle_poisson(float(lam), seed, cell, step))
+
+
+def schwinger_pair_ids(seed: int, cell: int, step: int, j: int):
+    out = np.zeros(2, dtype=np.uint64)
+    lib().oracle_schwinger_pair_ids(seed, cell, step, j, _ptr(out))
+    return int(out[0]), int(out[1])
+
+
+def schwinger_cells(fields: dict, dv: float, dt: float, weight: float, seed: int, step: int):
+    """Per cell: the expected number of pairs of weight `weight` and the drawn count."""
+    arrs = [_f64(fields[k]) for k in ("ex", "ey", "ez", "bx", "by", "bz")]
+    n = arrs[0].shape[0]
+    lam = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    lib().oracle_schwinger_cells(n, *[_ptr(a) for a in arrs], dv, dt, weight, seed, step, _ptr(lam), _ptr(cnt))
+    return lam, cnt
+
+
+def schwinger(fields: dict, dv: float, dt: float, weight: float, seed: int, step: int) -> dict:
+    """The pairs cells make in one step: per pair its cell, electron and
+    positron ids and optical depths (both at rest, with the cell's fields)."""
+    lam, cnt = schwinger_cells(fields, dv, dt, weight, seed, step)
+    cells, ide, idp = [], [], []
+    for c in np.nonzero(cnt)[0]:
+        for j in range(int(cnt[c])):
+            a, b = schwinger_pair_ids(seed, int(c), step, j)
+            cells.append(int(c)), ide.append(a), idp.append(b)
+    ide = np.array(ide, dtype=np.uint64)
+    idp = np.array(idp, dtype=np.uint64)
+    return {"lambda": lam, "count": cnt, "cell": np.array(cells, dtype=np.int64), "e_id": ide, "p_id": idp,
+            "e_tau": init_tau(ide, seed, step), "p_tau": init_tau(idp, seed, step)}

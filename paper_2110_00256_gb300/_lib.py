@@ -22,7 +22,7 @@ QED_EVOLVE_DEFAULT, QED_EVOLVE_DIRECT, QED_EVOLVE_BULK = 0, 1, 2
 QED_MAX_TABLE_N = 1024
 (QED_STAT_QS_EVENTS, QED_STAT_BW_EVENTS, QED_STAT_PHOTONS_KEPT, QED_STAT_PHOTONS_DISCARDED,
  QED_STAT_PAIRS, QED_STAT_BW_NO_PAIR, QED_STAT_DROPPED_CAPACITY, QED_STAT_NONFINITE,
- QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_COUNT) = range(11)
+ QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_SCHWINGER_PAIRS, QED_STAT_COUNT) = range(12)
 
 
 class QedError(RuntimeError):
@@ -59,6 +59,14 @@ class PlaneWave(C.Structure):
 
 class Patch(C.Structure):
     _fields_ = [("electrons", Species), ("positrons", Species), ("photons", Species), ("fire", FireList * 3)]
+
+
+class Cells(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("ex", "ey", "ez", "bx", "by", "bz", "x", "y", "z")] + [("n", C.c_int64)]
+
+
+class UnitScales(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("length", "time", "momentum", "energy", "e_field", "b_field")]
 
 
 class SubstepOpts(C.Structure):
@@ -100,6 +108,12 @@ SIGNATURES = {
     "qed_tune_evolve": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float), _P]),
     "qed_push_plane_wave": (_S, [C.POINTER(Species), _D, C.POINTER(PlaneWave), _D, _D, _S, _P]),
     "qed_push_stored_fields": (_S, [C.POINTER(Species), _D, _D, _S, _P]),
+    "qed_units_library": (_S, [C.POINTER(UnitScales)]),
+    "qed_schwinger_pairs": (_S, [C.POINTER(Cells), _D, _D, _D, _U64, _I64, C.POINTER(Species), C.POINTER(Species),
+                                 _S, _P, _P]),
+    "qed_units_reference_frequency": (_S, [_D, C.POINTER(UnitScales)]),
+    "qed_units_reference_length": (_S, [_D, C.POINTER(UnitScales)]),
+    "qed_units_heaviside_lorentz_mev": (_S, [C.POINTER(UnitScales)]),
     "qed_push_substep_batched": (_S, [_P, _P, C.POINTER(PlaneWave), _D, _D, _U64, _I64, C.POINTER(SubstepOpts), _S,
                                       _P]),
     "qed_push_batched": (_S, [_P, C.POINTER(PlaneWave), _D, _D, _I64, _P, _P]),

@@ -24,6 +24,7 @@ __all__ = [
     "qed_evolve_optical_depth", "qed_generate_photons", "qed_generate_pairs", "qed_substep",
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
     "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields", "qed_push_substep_batched",
+    "qed_schwinger_pairs",
     "qed_push_batched",
 ]
 
@@ -189,7 +190,7 @@ class Stats:
     """Device counters (QED_STAT_*)."""
 
     NAMES = ("qs_events", "bw_events", "photons_kept", "photons_discarded", "pairs", "bw_no_pair",
-             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout")
+             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout", "schwinger_pairs")
 
     def __init__(self, device="cuda"):
         self.t = torch.zeros(QED_STAT_COUNT, dtype=torch.int64, device=device)
@@ -398,6 +399,21 @@ def qed_push_substep_batched(t: Tables, b: Batch, wave, t0: float, dt: float, se
     check(lib().qed_push_substep_batched(t.handle, b.handle, C.byref(wave), float(t0), float(dt), int(seed), int(step),
                                          C.byref(opts) if opts is not None else None, 1 if store_fields else 0,
                                          _stream(stream)))
+
+
+def qed_schwinger_pairs(fields: dict, dv: float, dt: float, weight: float, seed: int, step: int,
+                        electrons: SpeciesBuffers, positrons: SpeciesBuffers, stats: Stats | None = None,
+                        positions: dict | None = None, stream=None):
+    """Schwinger pairs made in the cells whose fields (device tensors ex .. bz,
+    one entry per cell, the species' precision) are given (include/qed.h)."""
+    n = int(fields["ex"].numel())
+    ptr = lambda d, k: d[k].data_ptr() if d is not None else None  # noqa: E731
+    cells = _lib.Cells(*[fields[k].data_ptr() for k in ("ex", "ey", "ez", "bx", "by", "bz")],
+                       ptr(positions, "x"), ptr(positions, "y"), ptr(positions, "z"), n)
+    e, p = electrons.struct(), positrons.struct()
+    check(lib().qed_schwinger_pairs(C.byref(cells), float(dv), float(dt), float(weight), int(seed), int(step),
+                                    C.byref(e), C.byref(p), electrons.prec,
+                                    stats.t.data_ptr() if stats is not None else None, _stream(stream)))
 
 
 def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:

@@ -1,0 +1,215 @@
+// schwinger.cu -- Schwinger pair production per cell (§2.3, Eq. (shw)).  In
+// normalised units (c = 1, fields in E_s) the rate per unit volume and time is
+// eps eta coth(pi eta / eps) exp(-pi / eps) / (4 pi^2), in units of
+// 1/(lambda_C^3 t_C), with eps, eta from the field invariants F = (E^2 - B^2)/2
+// and G = E.B.  Each cell draws a Poisson number of pairs of weight w with mean
+// rate dV dt / w (inversion for means up to 100, else the normal approximation
+// by Box-Muller; one Philox draw, counter (cell, step, 4)); the pairs start at
+// rest with the cell's fields (and position), ids from Philox (cell, step,
+// 5 + 256 j) and optical depths from their ids.  The rate and the mean are
+// evaluated in FP64 at either storage precision, so that the integer counts do
+// not depend on it.
+#include <cmath>
+
+#include "common.cuh"
+#include "physics.cuh"
+
+namespace qed {
+
+int sm_count();
+
+constexpr uint32_t kPoisson = 4u, kPairIds = 5u;
+constexpr double kPi = 3.141592653589793;
+
+__device__ __forceinline__ double schwinger_rate(double ex, double ey, double ez, double bx, double by, double bz)
+{
+    const double F = 0.5 * ((ex * ex + ey * ey + ez * ez) - (bx * bx + by * by + bz * bz));
+    const double G = ex * bx + ey * by + ez * bz;
+    const double r = sqrt(F * F + G * G);
+    const double eps = sqrt(r + F);
+    const double eta = sqrt(r - F > 0.0 ? r - F : 0.0);
+    if (!(eps > 0.0)) return 0.0;
+    const double x = kPi * eta / eps;  // eta coth(pi eta / eps) = (eps / pi) x coth x
+    const double xcothx = x < 1e-8 ? 1.0 : x / tanh(x);
+    return eps * (eps / kPi) * xcothx * exp(-kPi / eps) / (4.0 * kPi * kPi);
+}
+
+__device__ __forceinline__ long long poisson_draw(double lambda, uint64_t seed, uint64_t cell, int64_t step)
+{
+    if (!(lambda > 0.0)) return 0;
+    const U4 w = draw(seed, cell, step, kPoisson);
+    const double u = uniform53(w.x, w.y);
+    if (lambda <= 100.0) {
+        double p = exp(-lambda), cdf = p;
+        long long k = 0;
+        while (u > cdf && k < 1000) {
+            ++k;
+            p *= lambda / (double)k;
+            cdf += p;
+        }
+        return k;
+    }
+    const double z = sqrt(-2.0 * log(u)) * cos(2.0 * kPi * uniform53(w.z, w.w));
+    const double k = floor(lambda + sqrt(lambda) * z + 0.5);
+    return k > 0.0 ? (long long)k : 0;
+}
+
+template <typename T>
+struct CellsView {
+    const T *ex, *ey, *ez, *bx, *by, *bz, *x, *y, *z;
+    int64_t n;
+};
+
+template <typename T>
+struct PairDest {
+    T *px, *py, *pz, *ex, *ey, *ez, *bx, *by, *bz, *tau, *tau_c, *w, *x, *y, *z;
+    uint64_t *id;
+    unsigned long long *count;
+    int64_t cap;
+};
+
+template <typename T>
+PairDest<T> pair_dest(const qed_species *s)
+{
+    return PairDest<T>{(T *)s->px, (T *)s->py, (T *)s->pz, (T *)s->ex, (T *)s->ey, (T *)s->ez,
+                       (T *)s->bx, (T *)s->by, (T *)s->bz, (T *)s->tau, (T *)s->tau_c, (T *)s->weight,
+                       (T *)s->x, (T *)s->y, (T *)s->z, s->id, (unsigned long long *)s->d_count,
+                       s->capacity};
+}
+
+template <typename T>
+__device__ __forceinline__ void put(const PairDest<T> &d, int64_t k, const CellsView<T> &c, int64_t cell, T weight,
+                                    uint64_t id, double tau)
+{
+    d.px[k] = T(0), d.py[k] = T(0), d.pz[k] = T(0);
+    d.ex[k] = c.ex[cell], d.ey[k] = c.ey[cell], d.ez[k] = c.ez[cell];
+    d.bx[k] = c.bx[cell], d.by[k] = c.by[cell], d.bz[k] = c.bz[cell];
+    d.w[k] = weight;
+    d.id[k] = id;
+    store_tau<T>(d.tau, d.tau_c, k, tau);
+    if (d.x && c.x) d.x[k] = c.x[cell], d.y[k] = c.y[cell], d.z[k] = c.z[cell];
+}
+
+// a slot reserved for a pair whose other half found no room
+template <typename T>
+__device__ __forceinline__ void put_dead(const PairDest<T> &d, int64_t k)
+{
+    d.px[k] = T(0), d.py[k] = T(0), d.pz[k] = T(0);
+    d.ex[k] = T(0), d.ey[k] = T(0), d.ez[k] = T(0), d.bx[k] = T(0), d.by[k] = T(0), d.bz[k] = T(0);
+    d.w[k] = T(0);
+    d.id[k] = ~0ull;
+    store_tau<T>(d.tau, d.tau_c, k, (double)INFINITY);
+    if (d.x) d.x[k] = T(0), d.y[k] = T(0), d.z[k] = T(0);
+}
+
+// warp-aggregated reservation of v slots per lane: one atomic per warp
+__device__ __forceinline__ long long warp_reserve_n(unsigned long long *counter, long long v)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return (long long)base + incl - v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
+                                                         uint64_t seed, int64_t step, PairDest<T> e, PairDest<T> p,
+                                                         long long *stats)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the reservation is warp-collective)
+    const int64_t n_pad = (c.n + 31) / 32 * 32;
+    int made = 0, dropped = 0;
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell - (threadIdx.x & 31) < n_pad;
+         cell += stride) {
+        long long k = 0;
+        if (cell < c.n) {
+            const double rate = schwinger_rate((double)c.ex[cell], (double)c.ey[cell], (double)c.ez[cell],
+                                               (double)c.bx[cell], (double)c.by[cell], (double)c.bz[cell]);
+            k = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)cell, step);
+        }
+        const long long se = warp_reserve_n(e.count, k);
+        const long long sp = warp_reserve_n(p.count, k);
+        for (long long j = 0; j < k; ++j) {
+            const bool ok_e = se + j < e.cap, ok_p = sp + j < p.cap;
+            if (ok_e && ok_p) {
+                const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)j);
+                const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
+                put<T>(e, se + j, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
+                put<T>(p, sp + j, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
+                ++made;
+            } else {
+                if (ok_e) put_dead<T>(e, se + j);
+                if (ok_p) put_dead<T>(p, sp + j);
+                ++dropped;
+            }
+        }
+    }
+    if (stats) {
+        warp_count(stats + QED_STAT_SCHWINGER_PAIRS, made);
+        warp_count(stats + QED_STAT_DROPPED_CAPACITY, dropped);
+    }
+}
+
+// the species' counts never pass their capacity
+__global__ void clamp_pair_counts(unsigned long long *a, int64_t ca, unsigned long long *b, int64_t cb)
+{
+    if (threadIdx.x == 0) {
+        if (*a > (unsigned long long)ca) *a = ca;
+        if (*b > (unsigned long long)cb) *b = cb;
+    }
+}
+
+template <typename T>
+static qed_status launch(const qed_cells *cells, double dv, double dt, double weight, uint64_t seed, int64_t step,
+                         const qed_species *el, const qed_species *po, int64_t *d_stats, cudaStream_t st)
+{
+    const CellsView<T> c{(const T *)cells->ex, (const T *)cells->ey, (const T *)cells->ez, (const T *)cells->bx,
+                         (const T *)cells->by, (const T *)cells->bz, (const T *)cells->x, (const T *)cells->y,
+                         (const T *)cells->z, cells->n};
+    int64_t grid = (cells->n + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
+    schwinger_kernel<T><<<(int)grid, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el),
+                                                   pair_dest<T>(po), (long long *)d_stats);
+    QED_LAUNCH_CHECK();
+    clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
+                                        (unsigned long long *)po->d_count, po->capacity);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" qed_status qed_schwinger_pairs(const qed_cells *cells, double dv, double dt, double weight, uint64_t seed,
+                                          int64_t step, const qed_species *electrons, const qed_species *positrons,
+                                          qed_precision prec, int64_t *d_stats, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if (!cells) QED_FAIL(QED_ERR_INVALID_ARG, "cells is NULL");
+    if (cells->n < 0) QED_FAIL(QED_ERR_INVALID_ARG, "negative number of cells");
+    if (cells->n > 0 && (!cells->ex || !cells->ey || !cells->ez || !cells->bx || !cells->by || !cells->bz))
+        QED_FAIL(QED_ERR_INVALID_ARG, "a cell field array is NULL");
+    if ((s = check_species(electrons, "electrons", prec))) return s;
+    if ((s = check_species(positrons, "positrons", prec))) return s;
+    if ((electrons->x || positrons->x) && cells->n > 0 && !cells->x)
+        QED_FAIL(QED_ERR_INVALID_ARG, "the species have positions: the cells need theirs");
+    if (!(dv > 0.0) || !(dt >= 0.0) || !(weight > 0.0) || !std::isfinite(dv) || !std::isfinite(dt) ||
+        !std::isfinite(weight))
+        QED_FAIL(QED_ERR_INVALID_ARG, "dv and weight must be > 0, dt >= 0");
+    if (cells->n == 0) return QED_OK;
+    cudaStream_t st = as_stream(stream);
+    return prec == QED_F32 ? launch<float>(cells, dv, dt, weight, seed, step, electrons, positrons, d_stats, st)
+                           : launch<double>(cells, dv, dt, weight, seed, step, electrons, positrons, d_stats, st);
+}
