@@ -84,10 +84,11 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record():
-    """DRAM bytes per particle of the evolution kernel from the committed ncu
-    summary, valid only while the kernel's sources are unchanged."""
-    path = os.path.join(ROOT, "profiles", "evolve_kernel_fp32_traffic.txt")
+def profile_record(name: str, key: str):
+    """A per-particle figure of the evolution kernel from a committed ncu
+    summary (profiles/<name>), valid only while the kernel's sources are
+    unchanged."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         rec = {}
         for line in open(path):
@@ -96,9 +97,18 @@ def traffic_record():
                 rec[k.strip()] = v.strip()
         if rec.get("kernel_sources_sha256_16") != kernel_hash():
             return None
-        return float(rec["dram_bytes_per_particle"])
+        return float(rec[key])
     except Exception:
         return None
+
+
+def traffic_record():
+    """DRAM bytes per particle of the FP32 evolution kernel."""
+    return profile_record("evolve_kernel_fp32_traffic.txt", "dram_bytes_per_particle")
+
+
+# FP64 pipe of GB300: 2 thread instructions per SM per clock (profiles/evolve_kernel_fp64_pipe.md)
+FP64_INST_PER_SM_CLOCK = 2.0
 
 
 class Clocks:
@@ -429,6 +439,17 @@ def gpu_main(args):
                                           "ms_per_step": ms64 / max(3, args.steps // 4),
                                           "evolve_ms": round(ev64, 4), "hbm_gbs": round(ach64, 1),
                                           "hbm_frac": round(ach64 / hbm, 4)}}
+        ipp = profile_record("evolve_kernel_fp64_insts.txt", "fp64_inst_per_particle")
+        if ipp:
+            import torch as _t
+            peak64 = FP64_INST_PER_SM_CLOCK * _t.cuda.get_device_properties(0).multi_processor_count * \
+                (clk["sm_mhz"] if clk else 2070.0) * 1e6
+            ach_i = ipp * r64["n_before"] / (ev64 * 1e-3)
+            result["paths"]["fp64_table"]["roofline"] = {
+                "bound": "alu", "kernel": "evolve_kernel<double,2,4,3>", "unit": "FP64 instructions/s",
+                "achieved": ach_i, "peak": peak64, "frac": round(ach_i / peak64, 4),
+                "peak_kind": "2 FP64 instructions per SM per clock x SMs x the sampled SM clock",
+                "fp64_inst_per_particle": ipp}
         bufs, fire = b64, f64
         del b64, f64
         torch.cuda.empty_cache()

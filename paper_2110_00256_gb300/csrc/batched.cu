@@ -106,7 +106,7 @@ __device__ __forceinline__ int find_seg(const long long *s_end, int n_seg, long 
 
 // dynamic shared memory: [InferSmem if MLP][s_end n][s_n n]
 template <typename T, bool MLP, bool QS>
-__global__ void __launch_bounds__(256) event_batched_kernel(const EventSeg<T> *__restrict__ segs, int n_seg,
+__global__ void __launch_bounds__(256, (MLP || sizeof(T) == 8) ? 1 : 4) event_batched_kernel(const EventSeg<T> *__restrict__ segs, int n_seg,
                                                             const __grid_constant__ EventCommon<T> c)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -132,34 +132,45 @@ __global__ void __launch_bounds__(256) event_batched_kernel(const EventSeg<T> *_
     flush_counts(c.stats, k, QS);
 }
 
+// CTAs of 256 threads for `warps` warp chunks of work, at most the resident count
+static int resident_grid(int64_t warps, int per_sm)
+{
+    int64_t grid = (warps + 7) / 8;
+    const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+    return (int)(grid < 1 ? 1 : (grid > cap ? cap : grid));
+}
+
 template <typename T, bool QS>
 static qed_status launch_events_batched(const qed_batch *b, const EventCommon<T> &c, bool mlp, cudaStream_t st)
 {
     const int n_seg = QS ? 2 * b->n_patches : b->n_patches;
     const EventSeg<T> *segs = (const EventSeg<T> *)(QS ? b->d_qs : b->d_bw);
     const size_t dyn = (mlp ? sizeof(InferSmem) : 0) + (size_t)n_seg * 2 * sizeof(long long);
-    int64_t warps = (b->fire_capacity_max * (QS ? 2 : 1) + 31) / 32;
-    int64_t grid = (warps + 7) / 8;
-    const int64_t cap = (int64_t)sm_count() * 4;
-    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
-    // the opt-in shared-memory size is set once, for the largest batch
+    const int64_t warps = (b->fire_capacity_max * (QS ? 2 : 1) + 31) / 32;
+    // the opt-in shared-memory size is set once, for the largest batch; the grid
+    // is at most what stays resident (every CTA strides over the chunks)
     constexpr int kMaxDyn = (int)sizeof(InferSmem) + 2 * QED_MAX_PATCHES * 2 * (int)sizeof(long long);
     if (mlp) {
         auto k = event_batched_kernel<T, true, QS>;
         static bool attr = false;
+        static int per_sm = 0;
         if (!attr) {
             QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            QED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, kMaxDyn));
             attr = true;
         }
-        k<<<(int)grid, 256, dyn, st>>>(segs, n_seg, c);
+        k<<<resident_grid(warps, per_sm), 256, dyn, st>>>(segs, n_seg, c);
     } else {
         auto k = event_batched_kernel<T, false, QS>;
         static bool attr = false;
+        static int per_sm = 0;
         if (!attr) {
             QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+            QED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 2 * QED_MAX_PATCHES * 2 *
+                                                                                      (int)sizeof(long long)));
             attr = true;
         }
-        k<<<(int)grid, 256, dyn, st>>>(segs, n_seg, c);
+        k<<<resident_grid(warps, per_sm), 256, dyn, st>>>(segs, n_seg, c);
     }
     QED_LAUNCH_CHECK();
     return QED_OK;

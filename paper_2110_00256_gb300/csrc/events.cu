@@ -73,11 +73,20 @@ __global__ void clamp_all(unsigned long long *s0, int64_t c0, unsigned long long
     }
 }
 
-static int event_grid(int64_t fire_cap)
+// CTAs of 256 threads for a firing list of fire_cap entries (a warp per chunk
+// of 32), at most as many as stay resident: every CTA strides over the chunks,
+// so a CTA that has to wait for a second wave only lengthens the launch
+template <auto Kernel>
+static int event_grid(size_t dyn, int64_t fire_cap)
 {
+    static int per_sm = 0;  // one per kernel
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, 256, dyn);
+        if (per_sm <= 0) per_sm = 1;
+    }
     int64_t warps = (fire_cap + 31) / 32;
     int64_t blocks = (warps + 7) / 8;
-    const int64_t cap = (int64_t)sm_count() * 4;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
     return (int)blocks;
 }
@@ -130,9 +139,11 @@ static qed_status launch_photons(const qed_tables *t, const qed_species *lep, co
             if (s) return s;
             attr = true;
         }
-        qs_event_kernel<T, true><<<event_grid(fire->capacity), 256, sizeof(InferSmem), st>>>(a);
+        qs_event_kernel<T, true>
+            <<<event_grid<qs_event_kernel<T, true>>(sizeof(InferSmem), fire->capacity), 256, sizeof(InferSmem), st>>>(
+                a);
     } else {
-        qs_event_kernel<T, false><<<event_grid(fire->capacity), 256, 0, st>>>(a);
+        qs_event_kernel<T, false><<<event_grid<qs_event_kernel<T, false>>(0, fire->capacity), 256, 0, st>>>(a);
     }
     QED_LAUNCH_CHECK();
     if (clamp) {
@@ -165,9 +176,11 @@ static qed_status launch_pairs(const qed_tables *t, const qed_species *ph, const
             if (s) return s;
             attr = true;
         }
-        bw_event_kernel<T, true><<<event_grid(fire->capacity), 256, sizeof(InferSmem), st>>>(a);
+        bw_event_kernel<T, true>
+            <<<event_grid<bw_event_kernel<T, true>>(sizeof(InferSmem), fire->capacity), 256, sizeof(InferSmem), st>>>(
+                a);
     } else {
-        bw_event_kernel<T, false><<<event_grid(fire->capacity), 256, 0, st>>>(a);
+        bw_event_kernel<T, false><<<event_grid<bw_event_kernel<T, false>>(0, fire->capacity), 256, 0, st>>>(a);
     }
     QED_LAUNCH_CHECK();
     if (clamp) {

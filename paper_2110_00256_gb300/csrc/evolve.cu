@@ -11,6 +11,7 @@
 // one index space; CTAs stride over it, so uneven segment sizes share the grid.
 #include <algorithm>
 
+#include "launch.cuh"
 #include "evolve_core.cuh"
 #include "pipeline.cuh"
 
@@ -493,14 +494,11 @@ extern "C" qed_status qed_init_optical_depth(const qed_species *sp, qed_precisio
     qed_status s = check_species(sp, "species", prec);
     if (s) return s;
     cudaStream_t st = as_stream(stream);
-    int64_t g = (sp->capacity + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    g = g < 1 ? 1 : (g > cap ? cap : g);
     if (prec == QED_F32)
-        init_tau_kernel<float><<<(int)g, 256, 0, st>>>((float *)sp->tau, (float *)sp->tau_c, sp->id, sp->d_count,
+        init_tau_kernel<float><<<resident_grid<init_tau_kernel<float>>(256, 0, sp->capacity), 256, 0, st>>>((float *)sp->tau, (float *)sp->tau_c, sp->id, sp->d_count,
                                                        sp->capacity, seed, step);
     else
-        init_tau_kernel<double><<<(int)g, 256, 0, st>>>((double *)sp->tau, nullptr, sp->id, sp->d_count,
+        init_tau_kernel<double><<<resident_grid<init_tau_kernel<double>>(256, 0, sp->capacity), 256, 0, st>>>((double *)sp->tau, nullptr, sp->id, sp->d_count,
                                                         sp->capacity, seed, step);
     QED_LAUNCH_CHECK();
     return QED_OK;

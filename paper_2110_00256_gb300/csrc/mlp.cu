@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "launch.cuh"
 #include "mlp.cuh"
 #include "physics.cuh"
 
@@ -234,8 +235,6 @@ __global__ void table_sample_kernel(Table2D<T> tb, int proc, const double *__res
     }
 }
 
-int sm_count();
-
 static qed_status check_mlp(const qed_mlp *m, int proc)
 {
     if (!m) QED_FAIL(QED_ERR_INVALID_ARG, "mlp handle is NULL");
@@ -410,10 +409,8 @@ extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const d
         QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    int64_t blocks = (n + kInferThreads - 1) / kInferThreads;
-    const int64_t cap = (int64_t)sm_count() * 4;
-    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
-    mlp_sample_kernel<<<(int)blocks, kInferThreads, sm, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n, d_xi);
+    const int blocks = resident_grid<mlp_sample_kernel>(kInferThreads, sm, n);
+    mlp_sample_kernel<<<blocks, kInferThreads, sm, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n, d_xi);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
@@ -426,17 +423,14 @@ extern "C" qed_status qed_table_sample(const qed_tables *t, qed_process proc, qe
     if ((s = check_tables(t))) return s;
     if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", (int)proc);
     if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
-    int64_t blocks = (n + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
     cudaStream_t st = as_stream(stream);
     if (prec == QED_F32) {
         TablesView<float> v = make_view<float>(t);
-        table_sample_kernel<float><<<(int)blocks, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
+        table_sample_kernel<float><<<resident_grid<table_sample_kernel<float>>(256, 0, n), 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
                                                                 d_u, n, d_xi);
     } else {
         TablesView<double> v = make_view<double>(t);
-        table_sample_kernel<double><<<(int)blocks, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
+        table_sample_kernel<double><<<resident_grid<table_sample_kernel<double>>(256, 0, n), 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
                                                                  d_u, n, d_xi);
     }
     QED_LAUNCH_CHECK();

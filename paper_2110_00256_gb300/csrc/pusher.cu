@@ -10,11 +10,10 @@
 #include <cstring>
 #include <vector>
 
+#include "launch.cuh"
 #include "pusher.cuh"
 
 namespace qed {
-
-int sm_count();
 
 // momentum (Boris) and position update of particle i with the fields (ex .. bz)
 template <typename T>
@@ -137,10 +136,8 @@ qed_status launch_push(const void *d_segs, int n_seg, const WaveParams &w, doubl
                                           3 * QED_MAX_PATCHES * (int)sizeof(long long)));
         attr = true;
     }
-    int64_t grid = (capacity + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
-    push_kernel<T><<<(int)grid, 256, dyn, st>>>((const PushSeg<T> *)d_segs, n_seg, w, t0, dt, d_step, step);
+    push_kernel<T><<<resident_grid<push_kernel<T>>(256, 3 * QED_MAX_PATCHES * sizeof(long long), capacity), 256, dyn,
+                     st>>>((const PushSeg<T> *)d_segs, n_seg, w, t0, dt, d_step, step);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
@@ -178,13 +175,12 @@ extern "C" qed_status qed_push_plane_wave(const qed_species *sp, double charge, 
     if ((s = check_wave(wave))) return s;
     if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
     cudaStream_t st = as_stream(stream);
-    int64_t grid = (sp->capacity + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
     if (prec == QED_F32)
-        push_single_kernel<float><<<(int)grid, 256, 0, st>>>(push_seg<float>(sp, charge), wave_params(wave), t, dt);
+        push_single_kernel<float><<<resident_grid<push_single_kernel<float>>(256, 0, sp->capacity), 256, 0, st>>>(
+            push_seg<float>(sp, charge), wave_params(wave), t, dt);
     else
-        push_single_kernel<double><<<(int)grid, 256, 0, st>>>(push_seg<double>(sp, charge), wave_params(wave), t, dt);
+        push_single_kernel<double><<<resident_grid<push_single_kernel<double>>(256, 0, sp->capacity), 256, 0, st>>>(
+            push_seg<double>(sp, charge), wave_params(wave), t, dt);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
@@ -199,13 +195,12 @@ extern "C" qed_status qed_push_stored_fields(const qed_species *sp, double charg
     if (!std::isfinite(charge)) QED_FAIL(QED_ERR_INVALID_ARG, "charge must be finite");
     if (!std::isfinite(dt) || dt < 0) QED_FAIL(QED_ERR_INVALID_ARG, "dt must be finite and >= 0");
     cudaStream_t st = as_stream(stream);
-    int64_t grid = (sp->capacity + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
     if (prec == QED_F32)
-        push_stored_kernel<float><<<(int)grid, 256, 0, st>>>(push_seg<float>(sp, charge), dt);
+        push_stored_kernel<float><<<resident_grid<push_stored_kernel<float>>(256, 0, sp->capacity), 256, 0, st>>>(
+            push_seg<float>(sp, charge), dt);
     else
-        push_stored_kernel<double><<<(int)grid, 256, 0, st>>>(push_seg<double>(sp, charge), dt);
+        push_stored_kernel<double><<<resident_grid<push_stored_kernel<double>>(256, 0, sp->capacity), 256, 0, st>>>(
+            push_seg<double>(sp, charge), dt);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }

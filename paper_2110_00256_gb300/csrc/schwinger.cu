@@ -11,12 +11,11 @@
 // not depend on it.
 #include <cmath>
 
+#include "launch.cuh"
 #include "common.cuh"
 #include "physics.cuh"
 
 namespace qed {
-
-int sm_count();
 
 constexpr uint32_t kPoisson = 4u, kPairIds = 5u;
 constexpr double kPi = 3.141592653589793;
@@ -175,10 +174,7 @@ static qed_status launch(const qed_cells *cells, double dv, double dt, double we
     const CellsView<T> c{(const T *)cells->ex, (const T *)cells->ey, (const T *)cells->ez, (const T *)cells->bx,
                          (const T *)cells->by, (const T *)cells->bz, (const T *)cells->x, (const T *)cells->y,
                          (const T *)cells->z, cells->n};
-    int64_t grid = (cells->n + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
-    schwinger_kernel<T><<<(int)grid, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el),
+    schwinger_kernel<T><<<resident_grid<schwinger_kernel<T>>(256, 0, cells->n), 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el),
                                                    pair_dest<T>(po), (long long *)d_stats);
     QED_LAUNCH_CHECK();
     clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
