@@ -103,10 +103,15 @@ struct Table1D {
     int n;
 };
 
+// bins of the guide tables that bracket the inverse-CDF search
+constexpr int kGuideBins = 64;
+
 template <typename T>
 struct Table2D {
     const T *v;      // [n_chi][n_xi], ln P (QS) or P (BW)
     const T *dv;     // [n_chi][n_xi], v[n][m+1] - v[n][m] formed in FP64 (last column 0)
+    const int32_t *guide;  // [n_chi][kGuideBins + 1]: per row, the largest m with v[n][m] at or
+                           // below each edge of kGuideBins equal bins of the uniform draw r
     T ln_min, inv_d, chi_min, chi_max;
     T x0, dx;        // xi axis: QS ln xi_min and step in ln xi; BW 0 and step in xi
     int n_chi, n_xi;
@@ -160,6 +165,8 @@ struct qed_tables {
     // accuracy even where neighbouring table entries are close
     double *d_qs_dlnP, *d_bw_dP;
     float *f_qs_dlnP, *f_bw_dP;
+    // guide tables of the 2-D tables' inverse-CDF search, one per precision
+    int32_t *d_qs_guide, *d_bw_guide, *f_qs_guide, *f_bw_guide;
 };
 
 namespace qed {

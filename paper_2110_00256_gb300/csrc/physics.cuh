@@ -152,7 +152,7 @@ __device__ __forceinline__ T row_val(const T *r0, const T *r1, T w, int m)
 // r0, r1 are the two rows, off their offset (for the difference table)
 template <typename T>
 __device__ __forceinline__ void locate_2d(const Table2D<T> &tb, T chi, const T *&r0, const T *&r1, T &w,
-                                          size_t &off)
+                                          size_t &off, int &row)
 {
     T c = chi < tb.chi_min ? tb.chi_min : (chi > tb.chi_max ? tb.chi_max : chi);
     T t = (d_log(c) - tb.ln_min) * tb.inv_d;
@@ -160,6 +160,7 @@ __device__ __forceinline__ void locate_2d(const Table2D<T> &tb, T chi, const T *
     int n = (int)t;
     n = n > tb.n_chi - 2 ? tb.n_chi - 2 : n;
     w = t - T(n);
+    row = n;
     off = (size_t)n * tb.n_xi;
     r0 = tb.v + off;
     r1 = r0 + tb.n_xi;
@@ -167,10 +168,18 @@ __device__ __forceinline__ void locate_2d(const Table2D<T> &tb, T chi, const T *
 
 // largest m in [0, M-1] with P_m <= x on the interpolated row (binary search;
 // the row is non-decreasing), then clamped to [0, M-2]; m = 0 when x < P_0.
+// The search starts from the bracket that the guide tables of the two rows give
+// for bin b of the draw (both rows' answers, hence the interpolated row's, lie
+// between their guides at b and b + 1), widened by one entry on each side
+// against rounding at the edges.
 template <typename T>
-__device__ __forceinline__ int search_row(const T *r0, const T *r1, T w, int M, T x)
+__device__ __forceinline__ int search_row(const T *r0, const T *r1, T w, int M, T x, const int32_t *g0,
+                                          const int32_t *g1, int b)
 {
-    int lo = 0, hi = M;  // invariant: P_lo <= x (or lo == 0), P_hi > x (hi == M: sentinel)
+    const int a0 = __ldg(g0 + b), a1 = __ldg(g1 + b), c0 = __ldg(g0 + b + 1), c1 = __ldg(g1 + b + 1);
+    int lo = (a0 < a1 ? a0 : a1) - 1, hi = (c0 > c1 ? c0 : c1) + 2;
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > M ? M : hi;  // invariant: P_lo <= x (or lo == 0), P_hi > x (hi == M: sentinel)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (row_val(r0, r1, w, mid) <= x)
@@ -193,9 +202,13 @@ __device__ __forceinline__ T qs_sample_xi(const Table2D<T> &tb, T chi, T r)
     const T *r0, *r1;
     T w;
     size_t off;
-    locate_2d(tb, chi, r0, r1, w, off);
+    int row;
+    locate_2d(tb, chi, r0, r1, w, off, row);
     const T lr = d_log(r);
-    const int m = search_row(r0, r1, w, tb.n_xi, lr);
+    const int *g0 = tb.guide + (size_t)row * (kGuideBins + 1);
+    int b = (int)(r * T(kGuideBins));
+    b = b > kGuideBins - 1 ? kGuideBins - 1 : (b < 0 ? 0 : b);
+    const int m = search_row(r0, r1, w, tb.n_xi, lr, g0, g0 + kGuideBins + 1, b);
     const T p0 = row_val(r0, r1, w, m);
     const T dp = row_val(tb.dv + off, tb.dv + off + tb.n_xi, w, m);  // P_{m+1} - P_m
     const T x0 = tb.x0 + T(m) * tb.dx;
@@ -218,8 +231,12 @@ __device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, double u,
     const T *r0, *r1;
     T w;
     size_t off;
-    locate_2d(tb, chi, r0, r1, w, off);
-    const int m = search_row(r0, r1, w, tb.n_xi, r);
+    int row;
+    locate_2d(tb, chi, r0, r1, w, off, row);
+    const int *g0 = tb.guide + (size_t)row * (kGuideBins + 1);
+    int b = (int)(r * T(2 * kGuideBins));
+    b = b > kGuideBins - 1 ? kGuideBins - 1 : (b < 0 ? 0 : b);
+    const int m = search_row(r0, r1, w, tb.n_xi, r, g0, g0 + kGuideBins + 1, b);
     const T p0 = row_val(r0, r1, w, m);
     const T dp = row_val(tb.dv + off, tb.dv + off + tb.n_xi, w, m);
     const T x0 = T(m) * tb.dx;

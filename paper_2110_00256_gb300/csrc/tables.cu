@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "physics.cuh"
 
 namespace qed {
 
@@ -45,11 +46,42 @@ __global__ void to_f32_kernel(const double *__restrict__ in, float *__restrict__
         out[i] = __double2float_rn(in[i]);
 }
 
+// Guide table of one 2-D table: for row n and edge e of kGuideBins equal bins
+// of the draw r (QS: r in (0, 1], searched as ln r; BW: r in [0, 1/2]), the
+// largest m with v[n][m] <= edge (0 if none); edge 0 is -inf, the last +inf.
+// A draw in bin b then lies between the rows' guides at b and b + 1.
+template <typename T>
+__global__ void guide_kernel(const T *__restrict__ v, int n_xi, bool qs, int32_t *__restrict__ g)
+{
+    const int n = blockIdx.x, e = threadIdx.x;
+    if (e > kGuideBins) return;
+    int32_t out;
+    if (e == 0) {
+        out = 0;
+    } else if (e == kGuideBins) {
+        out = n_xi - 1;
+    } else {
+        const T x = qs ? d_log(T(e) / T(kGuideBins)) : T(e) / T(2 * kGuideBins);
+        const T *row = v + (size_t)n * n_xi;
+        int lo = 0, hi = n_xi;  // largest m with row[m] <= x: row[lo] <= x (or lo == 0), row[hi] > x
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (row[mid] <= x)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        out = lo;
+    }
+    g[(size_t)n * (kGuideBins + 1) + e] = out;
+}
+
 static void free_tables(qed_tables *t)
 {
     if (!t) return;
     void *ptrs[] = {t->d_qs_lnG, t->d_qs_lnP, t->d_bw_lnT, t->d_bw_P, t->f_qs_lnG, t->f_qs_lnP, t->f_bw_lnT, t->f_bw_P,
-                    t->d_qs_dlnP, t->d_bw_dP, t->f_qs_dlnP, t->f_bw_dP};
+                    t->d_qs_dlnP, t->d_bw_dP, t->f_qs_dlnP, t->f_bw_dP, t->d_qs_guide, t->d_bw_guide,
+                    t->f_qs_guide, t->f_bw_guide};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -75,11 +107,20 @@ qed_status alloc_tables(const qed_table_params *p, qed_tables **out)
             QED_FAIL(QED_ERR_CUDA, "table allocation failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
         }
     }
+    const size_t ng[2] = {(size_t)p->qs.n_chi * (kGuideBins + 1), (size_t)p->bw.n_chi * (kGuideBins + 1)};
+    int32_t **gp[4] = {&t->d_qs_guide, &t->f_qs_guide, &t->d_bw_guide, &t->f_bw_guide};
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t e = cudaMalloc((void **)gp[k], ng[k / 2] * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            free_tables(t);
+            QED_FAIL(QED_ERR_CUDA, "table allocation failed: %s", cudaGetErrorString(e));
+        }
+    }
     *out = t;
     return QED_OK;
 }
 
-// round the FP64 tables into the FP32 copies on `stream`
+// round the FP64 tables into the FP32 copies on `stream`, then the guides
 qed_status finish_tables(qed_tables *t, cudaStream_t st)
 {
     const qed_table_params &p = t->params;
@@ -96,6 +137,11 @@ qed_status finish_tables(qed_tables *t, cudaStream_t st)
         to_f32_kernel<<<blocks, 256, 0, st>>>(d[k], f[k], (int64_t)sz[k]);
         QED_LAUNCH_CHECK();
     }
+    guide_kernel<double><<<p.qs.n_chi, kGuideBins + 1, 0, st>>>(t->d_qs_lnP, p.qs.n_xi, true, t->d_qs_guide);
+    guide_kernel<float><<<p.qs.n_chi, kGuideBins + 1, 0, st>>>(t->f_qs_lnP, p.qs.n_xi, true, t->f_qs_guide);
+    guide_kernel<double><<<p.bw.n_chi, kGuideBins + 1, 0, st>>>(t->d_bw_P, p.bw.n_xi, false, t->d_bw_guide);
+    guide_kernel<float><<<p.bw.n_chi, kGuideBins + 1, 0, st>>>(t->f_bw_P, p.bw.n_xi, false, t->f_bw_guide);
+    QED_LAUNCH_CHECK();
     QED_CUDA_TRY(cudaStreamSynchronize(st));
     return QED_OK;
 }
@@ -115,11 +161,12 @@ static Table1D<T> view1(const T *f, const qed_table_axis &a)
 }
 
 template <typename T>
-static Table2D<T> view2(const T *f, const T *df, const qed_table_axis &a, bool qs)
+static Table2D<T> view2(const T *f, const T *df, const int32_t *guide, const qed_table_axis &a, bool qs)
 {
     Table2D<T> v;
     v.v = f;
     v.dv = df;
+    v.guide = guide;
     const double l0 = std::log(a.chi_min), l1 = std::log(a.chi_max);
     v.ln_min = (T)l0;
     v.inv_d = (T)((a.n_chi - 1) / (l1 - l0));
@@ -143,8 +190,8 @@ TablesView<double> make_view<double>(const qed_tables *t)
     TablesView<double> v;
     v.qs_G = view1<double>(t->d_qs_lnG, t->params.qs);
     v.bw_T = view1<double>(t->d_bw_lnT, t->params.bw);
-    v.qs_P = view2<double>(t->d_qs_lnP, t->d_qs_dlnP, t->params.qs, true);
-    v.bw_P = view2<double>(t->d_bw_P, t->d_bw_dP, t->params.bw, false);
+    v.qs_P = view2<double>(t->d_qs_lnP, t->d_qs_dlnP, t->d_qs_guide, t->params.qs, true);
+    v.bw_P = view2<double>(t->d_bw_P, t->d_bw_dP, t->d_bw_guide, t->params.bw, false);
     return v;
 }
 
@@ -154,8 +201,8 @@ TablesView<float> make_view<float>(const qed_tables *t)
     TablesView<float> v;
     v.qs_G = view1<float>(t->f_qs_lnG, t->params.qs);
     v.bw_T = view1<float>(t->f_bw_lnT, t->params.bw);
-    v.qs_P = view2<float>(t->f_qs_lnP, t->f_qs_dlnP, t->params.qs, true);
-    v.bw_P = view2<float>(t->f_bw_P, t->f_bw_dP, t->params.bw, false);
+    v.qs_P = view2<float>(t->f_qs_lnP, t->f_qs_dlnP, t->f_qs_guide, t->params.qs, true);
+    v.bw_P = view2<float>(t->f_bw_P, t->f_bw_dP, t->f_bw_guide, t->params.bw, false);
     return v;
 }
 
