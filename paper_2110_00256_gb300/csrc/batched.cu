@@ -106,8 +106,8 @@ __device__ __forceinline__ int find_seg(const long long *s_end, int n_seg, long 
 
 // dynamic shared memory: [InferSmem if MLP][s_end n][s_n n]
 template <typename T, bool MLP, bool QS>
-__global__ void __launch_bounds__(256, (MLP || sizeof(T) == 8) ? 1 : 4) event_batched_kernel(const EventSeg<T> *__restrict__ segs, int n_seg,
-                                                            const __grid_constant__ EventCommon<T> c)
+__global__ void __launch_bounds__(256, (MLP || sizeof(T) == 8) ? 1 : 4)
+    event_batched_kernel(const EventSeg<T> *__restrict__ segs, int n_seg, const __grid_constant__ EventCommon<T> c)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_warp[8];
@@ -316,7 +316,8 @@ extern "C" qed_status qed_batch_create(const qed_patch *patches, int32_t n_patch
     b->prec = prec;
     b->n_patches = n_patches;
     cudaStream_t st = as_stream(stream);
-    s = prec == QED_F32 ? build_batch<float>(patches, n_patches, b, st) : build_batch<double>(patches, n_patches, b, st);
+    s = prec == QED_F32 ? build_batch<float>(patches, n_patches, b, st)
+                        : build_batch<double>(patches, n_patches, b, st);
     if (s) {
         free_batch(b);
         return s;

@@ -494,12 +494,14 @@ extern "C" qed_status qed_init_optical_depth(const qed_species *sp, qed_precisio
     qed_status s = check_species(sp, "species", prec);
     if (s) return s;
     cudaStream_t st = as_stream(stream);
+    const int g = prec == QED_F32 ? resident_grid<init_tau_kernel<float>>(256, 0, sp->capacity)
+                                  : resident_grid<init_tau_kernel<double>>(256, 0, sp->capacity);
     if (prec == QED_F32)
-        init_tau_kernel<float><<<resident_grid<init_tau_kernel<float>>(256, 0, sp->capacity), 256, 0, st>>>((float *)sp->tau, (float *)sp->tau_c, sp->id, sp->d_count,
-                                                       sp->capacity, seed, step);
+        init_tau_kernel<float><<<g, 256, 0, st>>>((float *)sp->tau, (float *)sp->tau_c, sp->id, sp->d_count,
+                                                  sp->capacity, seed, step);
     else
-        init_tau_kernel<double><<<resident_grid<init_tau_kernel<double>>(256, 0, sp->capacity), 256, 0, st>>>((double *)sp->tau, nullptr, sp->id, sp->d_count,
-                                                        sp->capacity, seed, step);
+        init_tau_kernel<double><<<g, 256, 0, st>>>((double *)sp->tau, nullptr, sp->id, sp->d_count, sp->capacity,
+                                                   seed, step);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }

@@ -426,12 +426,14 @@ extern "C" qed_status qed_table_sample(const qed_tables *t, qed_process proc, qe
     cudaStream_t st = as_stream(stream);
     if (prec == QED_F32) {
         TablesView<float> v = make_view<float>(t);
-        table_sample_kernel<float><<<resident_grid<table_sample_kernel<float>>(256, 0, n), 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
-                                                                d_u, n, d_xi);
+        const int g = resident_grid<table_sample_kernel<float>>(256, 0, n);
+        table_sample_kernel<float><<<g, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi, d_u, n,
+                                                      d_xi);
     } else {
         TablesView<double> v = make_view<double>(t);
-        table_sample_kernel<double><<<resident_grid<table_sample_kernel<double>>(256, 0, n), 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi,
-                                                                 d_u, n, d_xi);
+        const int g = resident_grid<table_sample_kernel<double>>(256, 0, n);
+        table_sample_kernel<double><<<g, 256, 0, st>>>(proc == QED_PROC_QS ? v.qs_P : v.bw_P, proc, d_chi, d_u, n,
+                                                       d_xi);
     }
     QED_LAUNCH_CHECK();
     return QED_OK;

@@ -2,10 +2,11 @@
 // fields stored with the particles, to drive the QED substep in a cascade (the
 // paper's substep runs inside a PIC code; this is not from the paper).
 // Units: c = m_e = 1, momentum in m_e c, fields in E_s and E_s / c, time in
-// hbar/(m_e c^2), lengths in hbar/(m_e c); dp/dt = q (E + v x B).  Positions at t_n, momenta at t_{n+1/2}: fields at (x_n, t_n)
-// are written into the species' field arrays (where the substep reads them),
-// the momentum is advanced with the relativistic Boris rotation (J. P. Boris,
-// 1970) and the position with the new velocity; photons fly straight at c.
+// hbar/(m_e c^2), lengths in hbar/(m_e c); dp/dt = q (E + v x B).  Positions
+// at t_n, momenta at t_{n+1/2}: fields at (x_n, t_n) are written into the
+// species' field arrays (where the substep reads them), the momentum is
+// advanced with the relativistic Boris rotation (J. P. Boris, 1970) and the
+// position with the new velocity; photons fly straight at c.
 #include <cmath>
 #include <cstring>
 #include <vector>

@@ -131,9 +131,22 @@ __global__ void __launch_bounds__(256) schwinger_kernel(CellsView<T> c, double d
          cell += stride) {
         long long k = 0;
         if (cell < c.n) {
-            const double rate = schwinger_rate((double)c.ex[cell], (double)c.ey[cell], (double)c.ez[cell],
-                                               (double)c.bx[cell], (double)c.by[cell], (double)c.bz[cell]);
-            k = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)cell, step);
+            const T ex = c.ex[cell], ey = c.ey[cell], ez = c.ez[cell], bx = c.bx[cell], by = c.by[cell],
+                    bz = c.bz[cell];
+            // weak fields: exp(-pi/eps) underflows FP64 below eps = pi/745.13 = 0.00422
+            // (eps^2 = 1.78e-5), so the rate is exactly zero.  A FP32 estimate of
+            // eps^2 = sqrt(F^2 + G^2) + F, plus a bound on its rounding (1e-6 of E^2 + B^2),
+            // at or below 1e-5 skips the cell
+            const float e2 = (float)ex * (float)ex + (float)ey * (float)ey + (float)ez * (float)ez;
+            const float b2 = (float)bx * (float)bx + (float)by * (float)by + (float)bz * (float)bz;
+            const float g = (float)ex * (float)bx + (float)ey * (float)by + (float)ez * (float)bz;
+            const float f = 0.5f * (e2 - b2);
+            const float eps2 = sqrtf(f * f + g * g) + f;
+            if (!(eps2 + 1.0e-6f * (e2 + b2) <= 1.0e-5f)) {
+                const double rate = schwinger_rate((double)ex, (double)ey, (double)ez, (double)bx, (double)by,
+                                                   (double)bz);
+                k = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)cell, step);
+            }
         }
         const long long se = warp_reserve_n(e.count, k);
         const long long sp = warp_reserve_n(p.count, k);
@@ -174,8 +187,9 @@ static qed_status launch(const qed_cells *cells, double dv, double dt, double we
     const CellsView<T> c{(const T *)cells->ex, (const T *)cells->ey, (const T *)cells->ez, (const T *)cells->bx,
                          (const T *)cells->by, (const T *)cells->bz, (const T *)cells->x, (const T *)cells->y,
                          (const T *)cells->z, cells->n};
-    schwinger_kernel<T><<<resident_grid<schwinger_kernel<T>>(256, 0, cells->n), 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el),
-                                                   pair_dest<T>(po), (long long *)d_stats);
+    const int g = resident_grid<schwinger_kernel<T>>(256, 0, cells->n);
+    schwinger_kernel<T><<<g, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el), pair_dest<T>(po),
+                                           (long long *)d_stats);
     QED_LAUNCH_CHECK();
     clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
                                         (unsigned long long *)po->d_count, po->capacity);
