@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-schwinger", action="store_true")
     ap.add_argument("--cascade-scale", type=float, default=0.1,
                     help="fraction of the 64 patch counts round(10^(3+4U)) to run in the cascade leg")
     ap.add_argument("--cascade-steps", type=int, default=2000)
@@ -122,7 +123,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -358,6 +359,42 @@ def e2e_leg(api, t, bufs, fire, steps, ws):
     return ms, n_step, bi, bo
 
 
+def schwinger_leg(api, ws):
+    """Schwinger pairs per cell (qed_schwinger_pairs) on 1e8 FP32 cells: fields
+    of PIC strength (components N(0, 1e-3) E_s: the rate underflows, the FP32
+    pre-check skips the FP64 evaluation) and near-critical ones (N(0, 0.025)
+    E_s: every cell through the FP64 rate); cell volume (2.6e4 hbar/(m_e c))^3
+    (10 nm), dt = 1e3 hbar/(m_e c^2), pairs of weight 1."""
+    import torch
+    n = 100_000_000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    out = {}
+    for name, sigma in (("pic_fields", 1e-3), ("near_critical", 0.025)):
+        f = {k: torch.randn(n, generator=g, device="cuda", dtype=torch.float32) * sigma
+             for k in ("ex", "ey", "ez", "bx", "by", "bz")}
+        e = api.SpeciesBuffers(4_000_000, api.QED_F32)
+        p = api.SpeciesBuffers(4_000_000, api.QED_F32)
+        st = api.Stats()
+        ms = []
+        for rep in range(4):
+            e.count.zero_(), p.count.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            api.qed_schwinger_pairs(f, 1.7e13, 1e3, 1.0, 5, rep, e, p, stats=st)
+            b.record()
+            torch.cuda.synchronize()
+            if rep:
+                ms.append(a.elapsed_time(b))
+        m = sorted(ms)[len(ms) // 2]
+        out[name] = {"cells_per_s": n / (m * 1e-3), "ms": round(m, 4), "hbm_gbs": round(24 * n / (m * 1e-3) / 1e9, 1),
+                     "pairs_per_launch": st.as_dict()["schwinger_pairs"] / 4}
+        del f, e, p
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host cores, on a bounded sample of the workload."""
     import numpy as np
@@ -512,6 +549,9 @@ def gpu_main(args):
                              "workload": "64 patches, counts round(10^(3+4U)) x %g (seed 7), e- beam gamma 2000 +-5%% "
                                          "vs a0=100 linear plane wave (0.8 um), dt = T_L/200, photons < 2 m_e c^2 "
                                          "discarded" % args.cascade_scale}
+
+    if not args.no_schwinger:
+        result.setdefault("paths", {})["schwinger"] = schwinger_leg(api, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

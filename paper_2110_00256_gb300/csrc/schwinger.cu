@@ -101,6 +101,14 @@ __device__ __forceinline__ void put_dead(const PairDest<T> &d, int64_t k)
     if (d.x) d.x[k] = T(0), d.y[k] = T(0), d.z[k] = T(0);
 }
 
+// add per-lane 64-bit counts to a device counter, one atomic per warp
+__device__ __forceinline__ void warp_count64(long long *ctr, long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31u) == 0 && v) atomicAdd((unsigned long long *)ctr, (unsigned long long)v);
+}
+
 // warp-aggregated reservation of v slots per lane: one atomic per warp
 __device__ __forceinline__ long long warp_reserve_n(unsigned long long *counter, long long v)
 {
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(256) schwinger_kernel(CellsView<T> c, double d
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // whole warps iterate together (the reservation is warp-collective)
     const int64_t n_pad = (c.n + 31) / 32 * 32;
-    int made = 0, dropped = 0;
+    long long made = 0, dropped = 0;
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell - (threadIdx.x & 31) < n_pad;
          cell += stride) {
         long long k = 0;
@@ -150,24 +158,28 @@ __global__ void __launch_bounds__(256) schwinger_kernel(CellsView<T> c, double d
         }
         const long long se = warp_reserve_n(e.count, k);
         const long long sp = warp_reserve_n(p.count, k);
-        for (long long j = 0; j < k; ++j) {
-            const bool ok_e = se + j < e.cap, ok_p = sp + j < p.cap;
-            if (ok_e && ok_p) {
+        // slots [se, se + k) and [sp, sp + k); only those below the capacities exist,
+        // so the loop ends with the last of them whatever k is
+        const long long room_e = e.cap - se > 0 ? e.cap - se : 0, room_p = p.cap - sp > 0 ? p.cap - sp : 0;
+        const long long both = room_e < room_p ? room_e : room_p, any = room_e > room_p ? room_e : room_p;
+        const long long n_made = k < both ? k : both, n_touch = k < any ? k : any;
+        for (long long j = 0; j < n_touch; ++j) {
+            if (j < n_made) {
                 const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)j);
                 const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
                 put<T>(e, se + j, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
                 put<T>(p, sp + j, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
-                ++made;
-            } else {
-                if (ok_e) put_dead<T>(e, se + j);
-                if (ok_p) put_dead<T>(p, sp + j);
-                ++dropped;
+            } else {  // room in one species only: a placeholder there
+                if (j < room_e) put_dead<T>(e, se + j);
+                if (j < room_p) put_dead<T>(p, sp + j);
             }
         }
+        made += n_made;
+        dropped += k - n_made;
     }
     if (stats) {
-        warp_count(stats + QED_STAT_SCHWINGER_PAIRS, made);
-        warp_count(stats + QED_STAT_DROPPED_CAPACITY, dropped);
+        warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
+        warp_count64(stats + QED_STAT_DROPPED_CAPACITY, dropped);
     }
 }
 
