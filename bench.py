@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=N_PER_SPECIES, help="particles per species (electrons, photons)")
@@ -113,10 +113,14 @@ FP64_INST_PER_SM_CLOCK = 2.0
 
 
 class Clocks:
+    """nvidia-smi sampling of SM clock, power and throttle reasons every 20 ms,
+    started ahead of the timed region; stop() keeps the samples whose
+    timestamps fall inside [t0, t1] (host clock), the timed region."""
+
     def __init__(self, index: int):
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -124,10 +128,11 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
                                           "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(2.0)  # nvidia-smi takes a moment before its first sample
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float | None = None, t1: float | None = None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -136,24 +141,28 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1].split()[0]))
-                mx.append(float(parts[2].split()[0]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2].split()[0]), float(parts[3].split()[0]), parts[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names[1:], parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+        inside = [r for r in rows if t0 is None or (t0 - 0.025 <= r[0] <= t1 + 0.025)]
+        where = "timed region"
+        if not inside:  # the region was shorter than the sampling interval: the nearest sample
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:1] if rows else []
+            where = "nearest sample to the timed region"
+        if not inside:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "window": where}
 
 
 def barrier(ws):
@@ -223,6 +232,7 @@ def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=T
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize()
+    t0_host = time.time()
     t0.record(stream)
     for s in range(steps):
         if evolve_events:
@@ -231,11 +241,13 @@ def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=T
         call(step0 + warmup + s)
     t1.record(stream)
     torch.cuda.synchronize()
+    t1_host = time.time()
     barrier(ws)
     ms = t0.elapsed_time(t1)
     ev_ms = [a.elapsed_time(b) for a, b in evs] if evolve_events else []
     n_after = counts(bufs)
-    return dict(ms=ms, n_before=n_before, n_after=n_after, evolve_ms=ev_ms, stats=stats.as_dict())
+    return dict(ms=ms, n_before=n_before, n_after=n_after, evolve_ms=ev_ms, stats=stats.as_dict(), t0_host=t0_host,
+                t1_host=t1_host)
 
 
 def mlp_leg(api, tabs, bufs, fire, args, ws):
@@ -446,7 +458,7 @@ def gpu_main(args):
 
     clocks = Clocks(local)
     r = time_substep(api, tabs, bufs, fire, args.steps, args.warmup, ws)
-    clk = clocks.stop()
+    clk = clocks.stop(r["t0_host"], r["t1_host"])
 
     ms_max = max_over_ranks(ws, r["ms"])
     total = sum_over_ranks(ws, r["n_before"] * args.steps)
