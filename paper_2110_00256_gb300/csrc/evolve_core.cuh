@@ -65,13 +65,13 @@ __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_b
 {
     T chi, rate;
     if (proc == QED_PROC_QS) {
-        T gamma;
-        chi = chi_lepton(px, py, pz, ex, ey, ez, bx, by, bz, gamma);
-        rate = qs_rate(s_qs, tv.qs_G, chi, gamma);
+        T gamma, inv;
+        chi = chi_lepton(px, py, pz, ex, ey, ez, bx, by, bz, gamma, inv);
+        rate = qs_rate(s_qs, tv.qs_G, chi, gamma, inv);
     } else {
-        T pm;
-        chi = chi_photon(px, py, pz, ex, ey, ez, bx, by, bz, pm);
-        rate = bw_rate(s_bw, tv.bw_T, chi, pm);
+        T pm, inv;
+        chi = chi_photon(px, py, pz, ex, ey, ez, bx, by, bz, pm, inv);
+        rate = bw_rate(s_bw, tv.bw_T, chi, pm, inv);
     }
     const bool ok = isfinite(chi) && !isnan(tau) && isfinite(rate);
     bad += ok ? 0 : 1;

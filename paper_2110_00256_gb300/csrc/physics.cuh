@@ -33,10 +33,11 @@ constexpr double kTLarge = 0.37961230854357125;
 // chi = |E|.  FP64 keeps the difference form: its cancellation error, 1e-16
 // (S/chi)^2 relative, is below the FP64 tolerance, and it saves the FP64
 // square root and division of n, FP64 being GB300's scarce unit.
-// Returns chi and gamma; NaN inputs give NaN.
+// Returns chi, gamma and (FP64 only) 1/gamma; NaN inputs give NaN.
 __device__ __forceinline__ float chi_lepton(float px, float py, float pz, float ex, float ey, float ez, float bx,
-                                            float by, float bz, float &gamma)
+                                            float by, float bz, float &gamma, float &inv_gamma)
 {
+    inv_gamma = 0.0f;  // FP32 divides by gamma (see over())
     const float p2 = px * px + py * py + pz * pz;
     gamma = sqrtf(1.0f + p2);
     const float pm = sqrtf(p2);
@@ -50,10 +51,15 @@ __device__ __forceinline__ float chi_lepton(float px, float py, float pz, float 
     return sqrtf(s);
 }
 
+// FP64: gamma and 1/gamma from one reciprocal square root, so that the rate
+// multiplies instead of dividing (division and square root are the costliest
+// steps on GB300's FP64 pipe; rsqrt is within 1 ulp)
 __device__ __forceinline__ double chi_lepton(double px, double py, double pz, double ex, double ey, double ez,
-                                             double bx, double by, double bz, double &gamma)
+                                             double bx, double by, double bz, double &gamma, double &inv_gamma)
 {
-    gamma = sqrt(1.0 + (px * px + py * py + pz * pz));
+    const double g2 = 1.0 + (px * px + py * py + pz * pz);
+    inv_gamma = rsqrt(g2);
+    gamma = g2 * inv_gamma;
     const double fx = gamma * ex + (py * bz - pz * by);
     const double fy = gamma * ey + (pz * bx - px * bz);
     const double fz = gamma * ez + (px * by - py * bx);
@@ -64,10 +70,11 @@ __device__ __forceinline__ double chi_lepton(double px, double py, double pz, do
 
 // chi_gamma of a photon, §2 (gamma -> |p|, v -> c n).  FP32: | |p| E_perp + p x B |,
 // the perpendicular part of |p| E + p x B; FP64: the difference form.  Returns
-// chi and |p|.
+// chi, |p| and (FP64 only) 1/|p| (0 for p = 0).
 __device__ __forceinline__ float chi_photon(float px, float py, float pz, float ex, float ey, float ez, float bx,
-                                            float by, float bz, float &pm)
+                                            float by, float bz, float &pm, float &inv_pm)
 {
+    inv_pm = 0.0f;  // FP32 divides by |p|
     pm = sqrtf(px * px + py * py + pz * pz);
     const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
     const float nx = px * inv, ny = py * inv, nz = pz * inv;
@@ -79,9 +86,11 @@ __device__ __forceinline__ float chi_photon(float px, float py, float pz, float 
 }
 
 __device__ __forceinline__ double chi_photon(double px, double py, double pz, double ex, double ey, double ez,
-                                             double bx, double by, double bz, double &pm)
+                                             double bx, double by, double bz, double &pm, double &inv_pm)
 {
-    pm = sqrt(px * px + py * py + pz * pz);
+    const double p2 = px * px + py * py + pz * pz;
+    inv_pm = p2 > 0.0 ? rsqrt(p2) : 0.0;
+    pm = p2 * inv_pm;
     const double fx = pm * ex + (py * bz - pz * by);
     const double fy = pm * ey + (pz * bx - px * bz);
     const double fz = pm * ez + (px * by - py * bx);
@@ -105,20 +114,24 @@ __device__ __forceinline__ T interp_ln(const T *tab, T lc, T ln_min, T inv_d, in
     return d_fma(f, b - a, a);
 }
 
+// x / e: FP32 divides (IEEE); FP64 multiplies by the reciprocal inv = 1/e
+__device__ __forceinline__ float over(float x, float e, float) { return x / e; }
+__device__ __forceinline__ double over(double x, double, double inv) { return x * inv; }
+
 // QS rate (Eq. (qs_total_cross)): (2/3) alpha G(chi) / gamma; G clamped to the
 // end values outside [chi_min, chi_max] (§3.2); chi == 0 gives 0.
 template <typename T>
-__device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T gamma)
+__device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T gamma, T inv_gamma)
 {
     if (!(chi > T(0))) return T(0);
     const T lnG = interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n);
-    return T(2.0 / 3.0 * kAlpha) * d_exp(lnG) / gamma;
+    return over(T(2.0 / 3.0 * kAlpha) * d_exp(lnG), gamma, inv_gamma);
 }
 
 // BW rate (Eq. (bw_cross_tot)): alpha chi T(chi) / gamma_g; the asymptotes of
 // Eq. (t_func) outside [chi_min, chi_max] (§3.1).
 template <typename T>
-__device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T pm)
+__device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T pm, T inv_pm)
 {
     if (!(chi > T(0)) || !(pm > T(0))) return T(0);
     T Tv;
@@ -128,7 +141,7 @@ __device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T
         Tv = T(kTLarge) / d_cbrt(chi);
     else
         Tv = d_exp(interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n));
-    return T(kAlpha) * chi * Tv / pm;
+    return over(T(kAlpha) * chi * Tv, pm, inv_pm);
 }
 
 // uniform for sampling in the working precision: FP64 as drawn; FP32 rounded

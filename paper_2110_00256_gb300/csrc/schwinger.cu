@@ -126,56 +126,96 @@ __device__ __forceinline__ long long warp_reserve_n(unsigned long long *counter,
     return (long long)base + incl - v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
-                                                         uint64_t seed, int64_t step, PairDest<T> e, PairDest<T> p,
-                                                         long long *stats)
+// VEC consecutive cells per thread (16-byte loads when the arrays allow); a
+// warp whose cells make no pair skips the reservation
+template <typename T, int VEC>
+__device__ __forceinline__ void load_cells(const T *a, int64_t i0, int64_t n, bool vec, T (&v)[VEC])
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together (the reservation is warp-collective)
-    const int64_t n_pad = (c.n + 31) / 32 * 32;
+    if constexpr (VEC == 4) {
+        if (vec && i0 + 4 <= n) {
+            const float4 q = __ldcs(reinterpret_cast<const float4 *>(a + i0));
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+            return;
+        }
+    } else if constexpr (VEC == 2) {
+        if (vec && i0 + 2 <= n) {
+            const double2 q = __ldcs(reinterpret_cast<const double2 *>(a + i0));
+            v[0] = q.x, v[1] = q.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) v[j] = i0 + j < n ? a[i0 + j] : T(0);
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
+                                                            uint64_t seed, int64_t step, PairDest<T> e,
+                                                            PairDest<T> p, long long *stats, int vec)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * VEC;
     long long made = 0, dropped = 0;
-    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell - (threadIdx.x & 31) < n_pad;
-         cell += stride) {
-        long long k = 0;
-        if (cell < c.n) {
-            const T ex = c.ex[cell], ey = c.ey[cell], ez = c.ez[cell], bx = c.bx[cell], by = c.by[cell],
-                    bz = c.bz[cell];
+    // whole warps iterate together (the reservation is warp-collective): the loop
+    // runs while the warp's first cell is in range
+    for (int64_t c0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * VEC; c0 - (int64_t)lane * VEC < c.n;
+         c0 += stride) {
+        T ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC];
+        load_cells<T, VEC>(c.ex, c0, c.n, vec, ex);
+        load_cells<T, VEC>(c.ey, c0, c.n, vec, ey);
+        load_cells<T, VEC>(c.ez, c0, c.n, vec, ez);
+        load_cells<T, VEC>(c.bx, c0, c.n, vec, bx);
+        load_cells<T, VEC>(c.by, c0, c.n, vec, by);
+        load_cells<T, VEC>(c.bz, c0, c.n, vec, bz);
+        long long k[VEC], tot = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            k[j] = 0;
+            if (c0 + j >= c.n) continue;
             // weak fields: exp(-pi/eps) underflows FP64 below eps = pi/745.13 = 0.00422
             // (eps^2 = 1.78e-5), so the rate is exactly zero.  A FP32 estimate of
             // eps^2 = sqrt(F^2 + G^2) + F, plus a bound on its rounding (1e-6 of E^2 + B^2),
             // at or below 1e-5 skips the cell
-            const float e2 = (float)ex * (float)ex + (float)ey * (float)ey + (float)ez * (float)ez;
-            const float b2 = (float)bx * (float)bx + (float)by * (float)by + (float)bz * (float)bz;
-            const float g = (float)ex * (float)bx + (float)ey * (float)by + (float)ez * (float)bz;
-            const float f = 0.5f * (e2 - b2);
+            const float fex = (float)ex[j], fey = (float)ey[j], fez = (float)ez[j];
+            const float fbx = (float)bx[j], fby = (float)by[j], fbz = (float)bz[j];
+            const float e2 = fex * fex + fey * fey + fez * fez, b2 = fbx * fbx + fby * fby + fbz * fbz;
+            const float g = fex * fbx + fey * fby + fez * fbz, f = 0.5f * (e2 - b2);
             const float eps2 = sqrtf(f * f + g * g) + f;
             if (!(eps2 + 1.0e-6f * (e2 + b2) <= 1.0e-5f)) {
-                const double rate = schwinger_rate((double)ex, (double)ey, (double)ez, (double)bx, (double)by,
-                                                   (double)bz);
-                k = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)cell, step);
+                const double rate = schwinger_rate((double)ex[j], (double)ey[j], (double)ez[j], (double)bx[j],
+                                                   (double)by[j], (double)bz[j]);
+                k[j] = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)(c0 + j), step);
             }
+            tot += k[j];
         }
-        const long long se = warp_reserve_n(e.count, k);
-        const long long sp = warp_reserve_n(p.count, k);
-        // slots [se, se + k) and [sp, sp + k); only those below the capacities exist,
-        // so the loop ends with the last of them whatever k is
-        const long long room_e = e.cap - se > 0 ? e.cap - se : 0, room_p = p.cap - sp > 0 ? p.cap - sp : 0;
-        const long long both = room_e < room_p ? room_e : room_p, any = room_e > room_p ? room_e : room_p;
-        const long long n_made = k < both ? k : both, n_touch = k < any ? k : any;
-        for (long long j = 0; j < n_touch; ++j) {
-            if (j < n_made) {
-                const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)j);
-                const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
-                put<T>(e, se + j, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
-                put<T>(p, sp + j, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
-            } else {  // room in one species only: a placeholder there
-                if (j < room_e) put_dead<T>(e, se + j);
-                if (j < room_p) put_dead<T>(p, sp + j);
+        if (!__any_sync(0xffffffffu, tot > 0)) continue;
+        const long long se = warp_reserve_n(e.count, tot);
+        const long long sp = warp_reserve_n(p.count, tot);
+        long long off = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const int64_t cell = c0 + j;
+            // slots [se + off, se + off + k) and [sp + off, ...); only those below the
+            // capacities exist, so the loop ends with the last of them whatever k is
+            const long long be = se + off, bp = sp + off;
+            const long long room_e = e.cap - be > 0 ? e.cap - be : 0, room_p = p.cap - bp > 0 ? p.cap - bp : 0;
+            const long long both = room_e < room_p ? room_e : room_p, any = room_e > room_p ? room_e : room_p;
+            const long long n_made = k[j] < both ? k[j] : both, n_touch = k[j] < any ? k[j] : any;
+            for (long long i = 0; i < n_touch; ++i) {
+                if (i < n_made) {
+                    const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)i);
+                    const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
+                    put<T>(e, be + i, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
+                    put<T>(p, bp + i, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
+                } else {  // room in one species only: a placeholder there
+                    if (i < room_e) put_dead<T>(e, be + i);
+                    if (i < room_p) put_dead<T>(p, bp + i);
+                }
             }
+            made += n_made;
+            dropped += k[j] - n_made;
+            off += k[j];
         }
-        made += n_made;
-        dropped += k - n_made;
     }
     if (stats) {
         warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
@@ -199,9 +239,13 @@ static qed_status launch(const qed_cells *cells, double dv, double dt, double we
     const CellsView<T> c{(const T *)cells->ex, (const T *)cells->ey, (const T *)cells->ez, (const T *)cells->bx,
                          (const T *)cells->by, (const T *)cells->bz, (const T *)cells->x, (const T *)cells->y,
                          (const T *)cells->z, cells->n};
-    const int g = resident_grid<schwinger_kernel<T>>(256, 0, cells->n);
-    schwinger_kernel<T><<<g, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el), pair_dest<T>(po),
-                                           (long long *)d_stats);
+    bool vec = true;
+    for (const void *a : {cells->ex, cells->ey, cells->ez, cells->bx, cells->by, cells->bz})
+        vec = vec && ((uintptr_t)a & 15u) == 0;
+    constexpr int V = sizeof(T) == 4 ? 4 : 2;
+    const int g = resident_grid<schwinger_kernel<T, V>>(256, 0, (cells->n + V - 1) / V);
+    schwinger_kernel<T, V><<<g, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el), pair_dest<T>(po),
+                                              (long long *)d_stats, vec ? 1 : 0);
     QED_LAUNCH_CHECK();
     clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
                                         (unsigned long long *)po->d_count, po->capacity);
