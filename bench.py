@@ -427,9 +427,20 @@ def cpu_baseline(seconds=12.0):
             break
     el = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 2 * m * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": 2 * m * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{2 * m} particles (paper §4 distribution, 256/256x256 FP64 oracle tables), {steps} substeps, "
                       f"{el:.1f} s wall; evolution OpenMP-parallel over particles, events serial"}
+
+
+def cpu_model() -> str:
+    """The host CPU as lscpu names it (model and architecture)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = dict(line.split(":", 1) for line in out.splitlines() if ":" in line)
+        name = info.get("Model name", "").strip() or info.get("Vendor ID", "").strip()
+        return f"{name} ({info.get('Architecture', '').strip()}, {info.get('CPU(s)', '').strip()} CPUs)"
+    except Exception:
+        return "unknown"
 
 
 def gpu_main(args):
@@ -607,7 +618,7 @@ def reference_main(args):
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
                       "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                       "sample": sample},
+                                       "cpu": cpu_model(), "sample": sample},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
           flush=True)
 
