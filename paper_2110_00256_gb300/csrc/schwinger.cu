@@ -148,10 +148,11 @@ __device__ __forceinline__ void load_cells(const T *a, int64_t i0, int64_t n, bo
     for (int j = 0; j < VEC; ++j) v[j] = i0 + j < n ? a[i0 + j] : T(0);
 }
 
+// ln_scale = ln(dv dt / (weight 4 pi^2)), in FP32 (+inf when it overflows)
 template <typename T, int VEC>
 __global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
                                                             uint64_t seed, int64_t step, PairDest<T> e,
-                                                            PairDest<T> p, long long *stats, int vec)
+                                                            PairDest<T> p, long long *stats, int vec, float ln_scale)
 {
     const unsigned lane = threadIdx.x & 31u;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * VEC;
@@ -172,16 +173,18 @@ __global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, doubl
         for (int j = 0; j < VEC; ++j) {
             k[j] = 0;
             if (c0 + j >= c.n) continue;
-            // weak fields: exp(-pi/eps) underflows FP64 below eps = pi/745.13 = 0.00422
-            // (eps^2 = 1.78e-5), so the rate is exactly zero.  A FP32 estimate of
-            // eps^2 = sqrt(F^2 + G^2) + F, plus a bound on its rounding (1e-6 of E^2 + B^2),
-            // at or below 1e-5 skips the cell
+            // Cells whose mean is below 2^-55 draw no pair whatever U (the largest
+            // uniform is 1 - 2^-54, below exp(-mean)).  A FP32 upper bound of the mean
+            // skips them: eps_up >= eps (eps^2 = sqrt(F^2 + G^2) + F plus a bound on its
+            // rounding, 1e-6 (E^2 + B^2)), eta coth(pi eta/eps) <= eta + eps/pi with
+            // eta <= sqrt(E^2 + B^2), and a margin of e^7 against FP32 rounding
             const float fex = (float)ex[j], fey = (float)ey[j], fez = (float)ez[j];
             const float fbx = (float)bx[j], fby = (float)by[j], fbz = (float)bz[j];
             const float e2 = fex * fex + fey * fey + fez * fez, b2 = fbx * fbx + fby * fby + fbz * fbz;
             const float g = fex * fbx + fey * fby + fez * fbz, f = 0.5f * (e2 - b2);
-            const float eps2 = sqrtf(f * f + g * g) + f;
-            if (!(eps2 + 1.0e-6f * (e2 + b2) <= 1.0e-5f)) {
+            const float eps_up = sqrtf(sqrtf(f * f + g * g) + f + 1.0e-6f * (e2 + b2));
+            const float ln_up = logf(eps_up * (sqrtf(e2 + b2) + eps_up)) - 3.14159274f / eps_up + ln_scale;
+            if (!(ln_up < -45.0f)) {  // -55 ln 2 = -38.1
                 const double rate = schwinger_rate((double)ex[j], (double)ey[j], (double)ez[j], (double)bx[j],
                                                    (double)by[j], (double)bz[j]);
                 k[j] = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)(c0 + j), step);
@@ -244,8 +247,10 @@ static qed_status launch(const qed_cells *cells, double dv, double dt, double we
         vec = vec && ((uintptr_t)a & 15u) == 0;
     constexpr int V = sizeof(T) == 4 ? 4 : 2;
     const int g = resident_grid<schwinger_kernel<T, V>>(256, 0, (cells->n + V - 1) / V);
+    const double ln_scale = std::log(dv * dt / (weight * 4.0 * kPi * kPi));
     schwinger_kernel<T, V><<<g, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el), pair_dest<T>(po),
-                                              (long long *)d_stats, vec ? 1 : 0);
+                                              (long long *)d_stats, vec ? 1 : 0,
+                                              ln_scale < 1e30 ? (float)ln_scale : INFINITY);
     QED_LAUNCH_CHECK();
     clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
                                         (unsigned long long *)po->d_count, po->capacity);
