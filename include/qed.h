@@ -424,7 +424,8 @@ qed_status qed_mlp_gradients(qed_mlp *m, qed_process proc, const double *d_chi, 
  * electron's chi_-/chi_g), device FP64 arrays. */
 qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
                           int64_t n, double *d_xi, void *stream);
-/* The same through the 2-D tables (§3.1, §3.2) in the given precision. */
+/* The same through the 2-D tables (§3.1, §3.2) in the given precision.  Both
+ * samplers accept n = 0 (nothing to do); training and gradients need n > 0. */
 qed_status qed_table_sample(const qed_tables *t, qed_process proc, qed_precision prec, const double *d_chi,
                             const double *d_u, int64_t n, double *d_xi, void *stream);
 

@@ -353,10 +353,11 @@ static qed_status launch_train(qed_mlp *m, int proc, const double *chi, const do
     return QED_OK;
 }
 
-static qed_status check_batch(const double *chi, const double *u, const double *xi, int64_t n)
+// training needs samples (empty = 0 allowed only where nothing is computed from them)
+static qed_status check_batch(const double *chi, const double *u, const double *xi, int64_t n, bool empty_ok = false)
 {
-    if (n <= 0) QED_FAIL(QED_ERR_INVALID_ARG, "batch size must be positive");
-    if (!chi || !u || !xi) QED_FAIL(QED_ERR_INVALID_ARG, "a batch array is NULL");
+    if (n < 0 || (n == 0 && !empty_ok)) QED_FAIL(QED_ERR_INVALID_ARG, "batch size must be positive");
+    if (n > 0 && (!chi || !u || !xi)) QED_FAIL(QED_ERR_INVALID_ARG, "a batch array is NULL");
     return QED_OK;
 }
 
@@ -402,7 +403,8 @@ extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const d
     clear_error();
     qed_status s;
     if ((s = check_mlp(m, proc))) return s;
-    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    if ((s = check_batch(d_chi, d_u, d_xi, n, true))) return s;
+    if (n == 0) return QED_OK;
     static bool attr = false;
     const size_t sm = sizeof(InferSmem);
     if (!attr) {
@@ -422,7 +424,8 @@ extern "C" qed_status qed_table_sample(const qed_tables *t, qed_process proc, qe
     qed_status s;
     if ((s = check_tables(t))) return s;
     if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", (int)proc);
-    if ((s = check_batch(d_chi, d_u, d_xi, n))) return s;
+    if ((s = check_batch(d_chi, d_u, d_xi, n, true))) return s;
+    if (n == 0) return QED_OK;
     cudaStream_t st = as_stream(stream);
     if (prec == QED_F32) {
         TablesView<float> v = make_view<float>(t);
