@@ -15,9 +15,11 @@
  *    enqueued and qed_last_error_message() (thread-local) says why.  No C++
  *    exception crosses this boundary.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
- *    stream).  Calls that take a stream only enqueue work and return without
- *    synchronising, unless stated otherwise; they never allocate device memory
- *    and are safe to capture in a CUDA graph.
+ *    stream).  The per-step calls (evolution, events, substeps, pushes,
+ *    Schwinger pairs, sampling, training steps) only enqueue work and return
+ *    without synchronising; they never allocate device memory and are safe to
+ *    capture in a CUDA graph.  Creating tables, batches and networks, and the
+ *    launch-shape tuner, allocate and/or synchronise, as stated with each.
  *  - Particle buffers are owned by the caller (device memory, structure of
  *    arrays).  Tables are owned by the library through an opaque handle.
  *  - A pointer documented as "device" must be device memory of the current

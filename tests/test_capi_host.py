@@ -85,7 +85,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
     from paper_2110_00256_gb300 import _lib
     pairs = {"qed_table_axis": _lib.TableAxis, "qed_table_params": _lib.TableParams, "qed_species": _lib.Species,
              "qed_fire_list": _lib.FireList, "qed_substep_opts": _lib.SubstepOpts, "qed_patch": _lib.Patch,
-             "qed_plane_wave": _lib.PlaneWave}
+             "qed_plane_wave": _lib.PlaneWave, "qed_cells": _lib.Cells, "qed_unit_scales": _lib.UnitScales}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qed.h"', 'int main(void) {']
     for cname, py in pairs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
@@ -104,3 +104,24 @@ def test_binding_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_enums_match_header(tmp_path):
+    """The status, statistics and evolution-variant constants of the binding
+    equal the header's."""
+    import subprocess
+    from paper_2110_00256_gb300 import _lib
+    names = [n for n in dir(_lib) if n.startswith(("QED_STAT_", "QED_EVOLVE_", "QED_MAX_", "QED_NOALLOC_"))
+             or n in ("QED_OK", "QED_F32", "QED_F64", "QED_PROC_QS", "QED_PROC_BW", "QED_MLP_PARAMS")]
+    lines = ['#include <stdio.h>', '#include "qed.h"', "int main(void) {"]
+    lines += ['printf("%s %%lld\\n", (long long)(%s));' % (n, n) for n in names]
+    lines += ["return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert len(names) >= 20
+    for n in names:
+        assert int(got[n]) == getattr(_lib, n), n
