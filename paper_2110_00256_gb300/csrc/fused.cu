@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
     for (int i = threadIdx.x; i < tab.qs_G.n; i += THREADS) s_qs[i] = tab.qs_G.ln_f[i];
     for (int i = threadIdx.x; i < tab.bw_T.n; i += THREADS) s_bw[i] = tab.bw_T.ln_f[i];
     const long long total = tile_prefix<T, THREADS>(segs, n_seg, tile, s_end, s_n, s_warp);
-    const double time = t0 + (double)(d_step ? *d_step : step) * dt_d;
+    const WaveT<T> wt = wave_at<T>(w, t0 + (double)(d_step ? *d_step : step) * dt_d);
     const T dt = (T)dt_d;
     int bad = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
         }
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-            wave_fields<T>(w, time, x[j], ex[j], ey[j], ez[j], bx[j], by[j], bz[j]);
+            wave_fields<T>(wt, x[j], ex[j], ey[j], ez[j], bx[j], by[j], bz[j]);
             T vx, vy, vz;
             boris_move<T>(pg.q, dt, ex[j], ey[j], ez[j], bx[j], by[j], bz[j], px[j], py[j], pz[j], vx, vy, vz);
             x[j] = x[j] + vx * dt;

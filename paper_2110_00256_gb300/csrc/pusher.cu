@@ -32,11 +32,11 @@ __device__ __forceinline__ void advance(const PushSeg<T> &g, int64_t i, T x, T e
 
 // plane wave: fields at (x_n, t_n) are written into the species, then the step
 template <typename T>
-__device__ __forceinline__ void push_one(const PushSeg<T> &g, int64_t i, const WaveParams &w, double t, T dt)
+__device__ __forceinline__ void push_one(const PushSeg<T> &g, int64_t i, const WaveT<T> &w, T dt)
 {
     const T x = g.x[i];
     T ex, ey, ez, bx, by, bz;
-    wave_fields<T>(w, t, x, ex, ey, ez, bx, by, bz);
+    wave_fields<T>(w, x, ex, ey, ez, bx, by, bz);
     g.ex[i] = ex, g.ey[i] = ey, g.ez[i] = ez, g.bx[i] = bx, g.by[i] = by, g.bz[i] = bz;
     advance<T>(g, i, x, ex, ey, ez, bx, by, bz, dt);
 }
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) push_kernel(const PushSeg<T> *__restrict_
     }
     __syncthreads();
     const long long total = s_dyn[n_seg - 1];
-    const double t = t0 + (double)(d_step ? *d_step : step) * dt;
+    const WaveT<T> wt = wave_at<T>(w, t0 + (double)(d_step ? *d_step : step) * dt);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x) {
         int lo = 0, hi = n_seg - 1;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) push_kernel(const PushSeg<T> *__restrict_
             else
                 lo = mid + 1;
         }
-        push_one<T>(segs[lo], k - (lo ? s_dyn[lo - 1] : 0), w, t, (T)dt);
+        push_one<T>(segs[lo], k - (lo ? s_dyn[lo - 1] : 0), wt, (T)dt);
     }
 }
 
@@ -109,10 +109,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) push_single_kernel(const __grid_constant__ PushSeg<T> g, WaveParams w,
                                                           double t, double dt)
 {
+    const WaveT<T> wt = wave_at<T>(w, t);
     int64_t n = *g.count;
     n = n < 0 ? 0 : (n > g.cap ? g.cap : n);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        push_one<T>(g, i, w, t, (T)dt);
+        push_one<T>(g, i, wt, (T)dt);
 }
 
 // fields already stored in the species (uniform fields, or gathered by the caller)

@@ -24,23 +24,35 @@ struct PushSeg {
 __device__ __forceinline__ void d_sincospi(float u, float *s, float *c) { sincospif(u, s, c); }
 __device__ __forceinline__ void d_sincospi(double u, double *s, double *c) { sincospi(u, s, c); }
 
+// the wave's parameters and the time in the working precision, converted once
+// per thread (conversions from FP64 run on GB300's narrow FP64 pipe)
+template <typename T>
+struct WaveT {
+    T omega_pi, phase0_pi, e0, d, t;
+    int circular;
+};
+
+template <typename T>
+__device__ __forceinline__ WaveT<T> wave_at(const WaveParams &w, double t)
+{
+    return WaveT<T>{(T)w.omega_pi, (T)w.phase0_pi, (T)w.e0, (T)w.direction, (T)t, w.circular};
+}
+
 // phase phi = omega (t - d x) + phase0; E = E0 (0, cos phi, [sin phi]); B = d x-hat cross E.
 // Evaluated in the working precision, in half-turns (over the cascade's 10
 // periods the FP32 phase keeps ~1e-5 rad).
 template <typename T>
-__device__ __forceinline__ void wave_fields(const WaveParams &w, double t, T x, T &ex, T &ey, T &ez, T &bx, T &by,
-                                            T &bz)
+__device__ __forceinline__ void wave_fields(const WaveT<T> &w, T x, T &ex, T &ey, T &ez, T &bx, T &by, T &bz)
 {
-    const T d = (T)w.direction;
-    const T u = (T)w.omega_pi * ((T)t - d * x) + (T)w.phase0_pi;
+    const T u = w.omega_pi * (w.t - w.d * x) + w.phase0_pi;
     T s, c;
     d_sincospi(u, &s, &c);
     ex = T(0);
-    ey = (T)w.e0 * c;
-    ez = w.circular ? (T)w.e0 * s : T(0);
+    ey = w.e0 * c;
+    ez = w.circular ? w.e0 * s : T(0);
     bx = T(0);
-    by = -d * ez;
-    bz = d * ey;
+    by = -w.d * ez;
+    bz = w.d * ey;
 }
 
 // one step of the momentum of a particle of charge q (relativistic Boris
