@@ -112,7 +112,11 @@ enum {
                                         pipeline (never expected; the launch's results
                                         are then incomplete)                             */
     QED_STAT_SCHWINGER_PAIRS = 10,   /* pairs made by qed_schwinger_pairs                  */
-    QED_STAT_COUNT = 11
+    QED_STAT_EVOLVED = 11,           /* particles the batched calls (qed_substep_batched,
+                                        qed_push_substep_batched) evolved: each step adds
+                                        the live count of every species of every patch, so
+                                        the sum over steps is the particle-steps done     */
+    QED_STAT_COUNT = 12
 };
 
 typedef struct {

@@ -22,7 +22,8 @@ QED_EVOLVE_DEFAULT, QED_EVOLVE_DIRECT, QED_EVOLVE_BULK = 0, 1, 2
 QED_MAX_TABLE_N = 1024
 (QED_STAT_QS_EVENTS, QED_STAT_BW_EVENTS, QED_STAT_PHOTONS_KEPT, QED_STAT_PHOTONS_DISCARDED,
  QED_STAT_PAIRS, QED_STAT_BW_NO_PAIR, QED_STAT_DROPPED_CAPACITY, QED_STAT_NONFINITE,
- QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_SCHWINGER_PAIRS, QED_STAT_COUNT) = range(12)
+ QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_SCHWINGER_PAIRS, QED_STAT_EVOLVED,
+ QED_STAT_COUNT) = range(13)
 
 
 class QedError(RuntimeError):

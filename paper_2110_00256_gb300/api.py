@@ -190,7 +190,7 @@ class Stats:
     """Device counters (QED_STAT_*)."""
 
     NAMES = ("qs_events", "bw_events", "photons_kept", "photons_discarded", "pairs", "bw_no_pair",
-             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout", "schwinger_pairs")
+             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout", "schwinger_pairs", "evolved")
 
     def __init__(self, device="cuda"):
         self.t = torch.zeros(QED_STAT_COUNT, dtype=torch.int64, device=device)

@@ -102,11 +102,9 @@ def run(tables: api.Tables, steps: int = 2000, scale: float = 1.0, photon_factor
     ms = ev0.elapsed_time(ev1)
     n1 = live()
     s = stats.as_dict()
-    # particle-steps: every step evolves every live particle; the population grows
-    # by the appended photons and pairs, so the count is bracketed by n0 and n1
-    # per step; the photons appended are spread over the run
-    appended = s["photons_kept"] + 2 * s["pairs"]
-    particle_steps = n0 * steps + appended * steps / 2.0
+    # particle-steps: each step adds the live count of every species of every
+    # patch, as the evolution reads it, to the 'evolved' counter
+    particle_steps = s["evolved"]
     return {"patches": int(len(counts)), "electrons": int(counts.sum()), "steps": steps, "ms": ms,
             "particle_steps": particle_steps, "value": particle_steps / (ms * 1e-3), "n_start": n0, "n_end": n1,
             "graph_nodes_per_step": 5 if fused else 6, "capture_s": capture_s, "tuned": tuned, "stats": s,

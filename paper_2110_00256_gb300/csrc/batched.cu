@@ -46,9 +46,30 @@ struct qed_batch {
 
 namespace qed {
 
-__global__ void zero_counts_kernel(int64_t *const *p, int n)
+// one CTA of 256: zero the n firing counts; with stats, add the live counts of
+// the species (the first three of every six clamp entries), clamped as the
+// evolution clamps them, to QED_STAT_EVOLVED: the particles this step evolves
+__global__ void __launch_bounds__(256) zero_counts_kernel(int64_t *const *p, int n, const ClampEntry *e,
+                                                          int n_patches, long long *stats)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *p[i] = 0;
+    __shared__ long long s_sum[8];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) *p[i] = 0;
+    if (!stats) return;
+    long long live = 0;
+    for (int i = threadIdx.x; i < 3 * n_patches; i += blockDim.x) {
+        const ClampEntry &c = e[6 * (i / 3) + i % 3];
+        const long long v = (long long)*c.count;  // as the evolution reads it
+        live += v < 0 ? 0 : (v > c.cap ? c.cap : v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(0xffffffffu, live, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = live;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
+        atomicAdd((unsigned long long *)(stats + QED_STAT_EVOLVED), (unsigned long long)t);
+    }
 }
 
 __global__ void clamp_batch_kernel(const ClampEntry *e, int n, int64_t *step)
@@ -259,13 +280,13 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
                                        double t0 = 0.0, int store_fields = 0)
 {
     const int n = b->n_patches;
-    zero_counts_kernel<<<(3 * n + 255) / 256, 256, 0, st>>>(b->d_zero, 3 * n);
+    long long *stats = o ? (long long *)o->d_stats : nullptr;
+    zero_counts_kernel<<<1, 256, 0, st>>>(b->d_zero, 3 * n, b->d_clamp, n, stats);
     QED_LAUNCH_CHECK();
     const int threads = (o && o->evolve_threads) ? o->evolve_threads : (b->threads ? b->threads : 256);
     const int ctas = (o && o->evolve_ctas_per_sm) ? o->evolve_ctas_per_sm : b->ctas_per_sm;
     if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
     const T cut_qs = o ? (T)o->qs_chi_cut : T(0), cut_bw = o ? (T)o->bw_chi_cut : T(0);
-    long long *stats = o ? (long long *)o->d_stats : nullptr;
     qed_status s = wave ? launch_push_evolve<T>((const EvolveSeg<T> *)b->d_evolve, b->d_push, 3 * n, make_view<T>(t),
                                                 wave_params(wave), t0, dt, o ? o->d_step : nullptr, step, cut_qs,
                                                 cut_bw, stats, store_fields, b->push_vec, st)

@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
     const WaveT<T> wt = wave_at<T>(w, t0 + (double)(d_step ? *d_step : step) * dt_d);
     const T dt = (T)dt_d;
     int bad = 0;
+    int s = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int s = find_segment(s_end, n_seg, t);
+        while (s_end[s] <= t) ++s;  // tiles ascend, so the segment (first s_end[s] > t) only moves forward
         const EvolveSeg<T> &sg = segs[s];
         const PushSeg<T> &pg = psegs[s];
         const int64_t n = s_n[s];

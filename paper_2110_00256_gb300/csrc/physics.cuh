@@ -13,8 +13,6 @@ __device__ __forceinline__ float d_exp(float x) { return expf(x); }
 __device__ __forceinline__ double d_exp(double x) { return exp(x); }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float d_cbrt(float x) { return cbrtf(x); }
-__device__ __forceinline__ double d_cbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float d_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double d_fma(double a, double b, double c) { return fma(a, b, c); }
 
@@ -24,6 +22,8 @@ __device__ __forceinline__ double d_fma(double a, double b, double c) { return f
 // Gamma(1/3)) for large chi.
 constexpr double kTSmall = 0.22963966338592293;
 constexpr double kTLarge = 0.37961230854357125;
+constexpr double kLnTSmall = -1.4712438795175893;  // ln kTSmall
+constexpr double kLnTLarge = -0.9686047877362934;  // ln kTLarge
 
 // chi of a lepton, §2: chi^2 = (gamma E + p x B)^2 - (p.E)^2 in these units.
 // FP32: with n = p/|p| and E_perp = E - (n.E) n the same quantity is the sum of
@@ -33,27 +33,27 @@ constexpr double kTLarge = 0.37961230854357125;
 // chi = |E|.  FP64 keeps the difference form: its cancellation error, 1e-16
 // (S/chi)^2 relative, is below the FP64 tolerance, and it saves the FP64
 // square root and division of n, FP64 being GB300's scarce unit.
-// Returns chi, gamma and (FP64 only) 1/gamma; NaN inputs give NaN.
+// gamma, 1/gamma, |p| and 1/|p| come from reciprocal square roots (rsqrtf within
+// 2 ulp, FP64 rsqrt within 1 ulp): the rate then multiplies instead of dividing,
+// and no IEEE division or square root but the last one of chi is left.
+// Returns chi, gamma and 1/gamma; NaN inputs give NaN.
 __device__ __forceinline__ float chi_lepton(float px, float py, float pz, float ex, float ey, float ez, float bx,
                                             float by, float bz, float &gamma, float &inv_gamma)
 {
-    inv_gamma = 0.0f;  // FP32 divides by gamma (see over())
     const float p2 = px * px + py * py + pz * pz;
-    gamma = sqrtf(1.0f + p2);
-    const float pm = sqrtf(p2);
-    const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
+    const float g2 = 1.0f + p2;
+    inv_gamma = rsqrtf(g2);
+    gamma = g2 * inv_gamma;
+    const float inv = p2 > 0.0f ? rsqrtf(p2) : 0.0f;
     const float nx = px * inv, ny = py * inv, nz = pz * inv;
     const float ne = nx * ex + ny * ey + nz * ez;
     const float fx = gamma * (ex - ne * nx) + (py * bz - pz * by);
     const float fy = gamma * (ey - ne * ny) + (pz * bx - px * bz);
     const float fz = gamma * (ez - ne * nz) + (px * by - py * bx);
-    const float s = fx * fx + fy * fy + fz * fz + (pm > 0.0f ? ne * ne : ex * ex + ey * ey + ez * ez);
+    const float s = fx * fx + fy * fy + fz * fz + (p2 > 0.0f ? ne * ne : ex * ex + ey * ey + ez * ez);
     return sqrtf(s);
 }
 
-// FP64: gamma and 1/gamma from one reciprocal square root, so that the rate
-// multiplies instead of dividing (division and square root are the costliest
-// steps on GB300's FP64 pipe; rsqrt is within 1 ulp)
 __device__ __forceinline__ double chi_lepton(double px, double py, double pz, double ex, double ey, double ez,
                                              double bx, double by, double bz, double &gamma, double &inv_gamma)
 {
@@ -70,14 +70,14 @@ __device__ __forceinline__ double chi_lepton(double px, double py, double pz, do
 
 // chi_gamma of a photon, §2 (gamma -> |p|, v -> c n).  FP32: | |p| E_perp + p x B |,
 // the perpendicular part of |p| E + p x B; FP64: the difference form.  Returns
-// chi, |p| and (FP64 only) 1/|p| (0 for p = 0).
+// chi, |p| and 1/|p| (0 for p = 0), from a reciprocal square root.
 __device__ __forceinline__ float chi_photon(float px, float py, float pz, float ex, float ey, float ez, float bx,
                                             float by, float bz, float &pm, float &inv_pm)
 {
-    inv_pm = 0.0f;  // FP32 divides by |p|
-    pm = sqrtf(px * px + py * py + pz * pz);
-    const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
-    const float nx = px * inv, ny = py * inv, nz = pz * inv;
+    const float p2 = px * px + py * py + pz * pz;
+    inv_pm = p2 > 0.0f ? rsqrtf(p2) : 0.0f;
+    pm = p2 * inv_pm;
+    const float nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
     const float ne = nx * ex + ny * ey + nz * ez;
     const float fx = pm * (ex - ne * nx) + (py * bz - pz * by);
     const float fy = pm * (ey - ne * ny) + (pz * bx - px * bz);
@@ -114,34 +114,33 @@ __device__ __forceinline__ T interp_ln(const T *tab, T lc, T ln_min, T inv_d, in
     return d_fma(f, b - a, a);
 }
 
-// x / e: FP32 divides (IEEE); FP64 multiplies by the reciprocal inv = 1/e
-__device__ __forceinline__ float over(float x, float e, float) { return x / e; }
-__device__ __forceinline__ double over(double x, double, double inv) { return x * inv; }
-
 // QS rate (Eq. (qs_total_cross)): (2/3) alpha G(chi) / gamma; G clamped to the
 // end values outside [chi_min, chi_max] (§3.2); chi == 0 gives 0.
 template <typename T>
-__device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T gamma, T inv_gamma)
+__device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T, T inv_gamma)
 {
     if (!(chi > T(0))) return T(0);
     const T lnG = interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n);
-    return over(T(2.0 / 3.0 * kAlpha) * d_exp(lnG), gamma, inv_gamma);
+    return T(2.0 / 3.0 * kAlpha) * d_exp(lnG) * inv_gamma;
 }
 
 // BW rate (Eq. (bw_cross_tot)): alpha chi T(chi) / gamma_g; the asymptotes of
-// Eq. (t_func) outside [chi_min, chi_max] (§3.1).
+// Eq. (t_func) outside [chi_min, chi_max] (§3.1).  All three branches give
+// ln T, so a warp whose photons straddle the table's ends runs one exponential:
+// ln T = ln(kTSmall) - 8 / (3 chi) below, ln(kTLarge) - (ln chi) / 3 above.
 template <typename T>
 __device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T pm, T inv_pm)
 {
     if (!(chi > T(0)) || !(pm > T(0))) return T(0);
-    T Tv;
+    const T lc = d_log(chi);
+    T lnT;
     if (chi < v.chi_min)
-        Tv = T(kTSmall) * d_exp(T(-8.0 / 3.0) / chi);
+        lnT = T(kLnTSmall) - T(8.0 / 3.0) / chi;
     else if (chi > v.chi_max)
-        Tv = T(kTLarge) / d_cbrt(chi);
+        lnT = d_fma(lc, T(-1.0 / 3.0), T(kLnTLarge));
     else
-        Tv = d_exp(interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n));
-    return over(T(kAlpha) * chi * Tv, pm, inv_pm);
+        lnT = interp_ln(tab, lc, v.ln_min, v.inv_d, v.n);
+    return T(kAlpha) * chi * d_exp(lnT) * inv_pm;
 }
 
 // uniform for sampling in the working precision: FP64 as drawn; FP32 rounded

@@ -78,8 +78,12 @@ def test_batched_equals_per_patch(api, tables, prec_name):
     b = api.Batch(bat, prec)
     api.qed_substep_batched(tables, b, 10.0, 3, 5, api.make_opts(stats=s_bat))
     torch.cuda.synchronize()
-    assert s_ref.as_dict() == s_bat.as_dict()
-    assert s_bat.as_dict()["qs_events"] > 0 and s_bat.as_dict()["pairs"] > 0
+    ref_stats, bat_stats = s_ref.as_dict(), s_bat.as_dict()
+    # the batched call also counts the particles it evolved: every live particle once
+    live = sum(len(h[k]["px"]) for h in host for k in SPECIES)
+    assert ref_stats.pop("evolved") == 0 and bat_stats.pop("evolved") == live
+    assert ref_stats == bat_stats
+    assert bat_stats["qs_events"] > 0 and bat_stats["pairs"] > 0
     for pa, pb in zip(ref, bat):
         _assert_same(pa, pb)
 
@@ -111,10 +115,17 @@ def test_graph_of_many_steps_equals_eager(api, tables):
     graph = _device_patches(api, host, api.QED_F32)
     be, bg = api.Batch(eager, api.QED_F32), api.Batch(graph, api.QED_F32)
     steps = 20
+    se = api.Stats()
+    live_sum = 0
     for s in range(steps):
-        api.qed_substep_batched(tables, be, 10.0, 9, s)
+        live_sum += sum(int(p[k].count.item()) for p in eager for k in SPECIES)
+        api.qed_substep_batched(tables, be, 10.0, 9, s, api.make_opts(stats=se))
+    torch.cuda.synchronize()
+    # the population grows with the photons and pairs appended; the counter follows it step by step
+    assert se.as_dict()["evolved"] == live_sum > steps * sum(len(h[k]["px"]) for h in host for k in SPECIES)
     d_step = torch.zeros(1, dtype=torch.int64, device="cuda")
-    opts = api.make_opts(d_step=d_step)
+    sg = api.Stats()
+    opts = api.make_opts(d_step=d_step, stats=sg)
     stream = torch.cuda.Stream()
     # first call outside the capture (sets the kernels' shared-memory limits)
     with torch.cuda.stream(stream):
@@ -133,6 +144,7 @@ def test_graph_of_many_steps_equals_eager(api, tables):
         g.replay()
     torch.cuda.synchronize()
     assert int(d_step.item()) == steps
+    assert sg.as_dict() == se.as_dict()
     for p in eager:
         for k in SPECIES:
             assert not np.any(_sorted(p[k])["id"] == np.uint64(0xFFFFFFFFFFFFFFFF))

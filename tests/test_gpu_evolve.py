@@ -166,3 +166,28 @@ def test_init_optical_depth_matches_oracle(api, prec_name):
     ref = oracle.init_tau(ids, 123456789, 7)
     # the FP32 pair (tau, tau_c) carries the FP64 value
     assert np.allclose(got, ref, rtol=1e-14 if prec_name == "f64" else 1e-13, atol=0)
+
+
+def test_bw_asymptotes_against_oracle(api):
+    """Breit-Wheeler rates below and above a narrow table (chi in [1, 10]) come
+    from the asymptotes of T (Eq. (t_func)); each photon's |p| is chosen so that
+    one step takes ~0.3 off its optical depth, so the rate itself is compared
+    (FP64 to 1e-12, FP32 to 1e-5 on tau)."""
+    ot = oracle.tables(qs_n_chi=32, qs_n_xi=32, bw_chi_min=1.0, bw_chi_max=10.0, bw_n_chi=32, bw_n_xi=32)
+    t = gpu_tables(api, ot)
+    chis = np.array([0.12, 0.2, 0.35, 0.6, 0.99, 1.0, 3.0, 10.0, 10.5, 40.0, 300.0, 5000.0])
+    n = len(chis)
+    z = np.zeros(n)
+    unit = dict(px=np.ones(n), py=z, pz=z, ex=z, ey=z, ez=z, bx=z, by=z, bz=chis.copy(), tau=np.ones(n),
+                tau_c=z, weight=np.ones(n), id=np.arange(n, dtype=np.uint64))
+    _, chi1, rate1, _ = oracle.evolve(1, ot, unit, 1.0)
+    assert np.allclose(chi1, chis, rtol=1e-15) and np.all(rate1 > 0)
+    pm = rate1 / 0.3  # rate = alpha chi T(chi) / |p|: a decrement of 0.3 at dt = 1
+    host = dict(unit, px=pm, bz=chis / pm)
+    for prec, dtype, tol in ((api.QED_F64, np.float64, 1e-12), (api.QED_F32, np.float32, 1e-5)):
+        got, fidx, _, st = _run(api, t, 1, host, prec, 1.0)
+        inp = as_f64(host, dtype)
+        tau_new, chi, rate, fire = oracle.evolve(1, ot, inp, 1.0)
+        assert np.all(np.abs(rate - 0.3) < 1e-3)
+        assert np.allclose(tau_eff(got, prec == api.QED_F32), tau_new, rtol=tol, atol=0)
+        assert len(fidx) == 0 and st["nonfinite"] == 0
