@@ -91,6 +91,41 @@ __device__ __forceinline__ bool evolve_one(int proc, const T *s_qs, const T *s_b
     }
 }
 
+// warp-ballot compaction of the firing particles among [i0, i0 + VEC) (cnt of
+// them in this thread) into the segment's firing list: one atomic per warp
+template <typename T, int VEC>
+__device__ __forceinline__ void compact_fire(const EvolveSeg<T> &sg, int64_t i0, const bool (&fire)[VEC],
+                                             const T (&chi)[VEC], int cnt, long long *stats)
+{
+    if (!__ballot_sync(0xffffffffu, cnt > 0)) return;
+    const unsigned lane = threadIdx.x & 31u;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(sg.fire_count, (unsigned long long)wtot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    long long pos = (long long)base + incl - cnt;
+    int over = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        if (fire[j]) {
+            if (pos < sg.fire_cap) {
+                sg.fire_idx[pos] = i0 + j;
+                sg.fire_chi[pos] = (double)chi[j];
+            } else {
+                ++over;
+            }
+            ++pos;
+        }
+    }
+    if (stats) warp_count(stats + QED_STAT_FIRE_OVERFLOW, over);
+}
+
 // Evaluate, store and compact VEC particles [i0, i0 + VEC) of segment `sg`
 // whose inputs are already in registers (full: all VEC are live).  dry != 0
 // evaluates everything but stores nothing (used by the launch-shape tuner).
@@ -102,7 +137,6 @@ __device__ __forceinline__ void evolve_regs(const EvolveSeg<T> &sg, int64_t n, i
                                             T (&tc)[VEC], const T *s_qs, const T *s_bw, const TablesView<T> &tab,
                                             T dt, T cut, long long *stats, int dry, int &bad)
 {
-    const unsigned lane = threadIdx.x & 31u;
     bool fire[VEC];
     T chi[VEC];
     int cnt = 0;
@@ -130,34 +164,7 @@ __device__ __forceinline__ void evolve_regs(const EvolveSeg<T> &sg, int64_t n, i
         }
     }
 
-    // warp-ballot compaction of the firing particles: one atomic per warp
-    if (__ballot_sync(0xffffffffu, cnt > 0)) {
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += v;
-        }
-        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31) base = atomicAdd(sg.fire_count, (unsigned long long)wtot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        long long pos = (long long)base + incl - cnt;
-        int over = 0;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            if (fire[j]) {
-                if (pos < sg.fire_cap) {
-                    sg.fire_idx[pos] = i0 + j;
-                    sg.fire_chi[pos] = (double)chi[j];
-                } else {
-                    ++over;
-                }
-                ++pos;
-            }
-        }
-        if (stats) warp_count(stats + QED_STAT_FIRE_OVERFLOW, over);
-    }
+    compact_fire<T, VEC>(sg, i0, fire, chi, cnt, stats);
 }
 
 // scalar loads of the live particles among [i0, i0 + VEC) (ragged tail, misaligned arrays)

@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
         const int64_t i0 = (t - (s ? s_end[s - 1] : 0)) * tile + (int64_t)threadIdx.x * VEC;
         const bool full = i0 + VEC <= n;
         T x[VEC], y[VEC], z[VEC], px[VEC], py[VEC], pz[VEC], tau[VEC], tc[VEC];
-        T ex[VEC], ey[VEC], ez[VEC], bx[VEC], by[VEC], bz[VEC];
         load_or_zero<T, VEC>(pg.x, i0, n, full, x);
         load_or_zero<T, VEC>(pg.y, i0, n, full, y);
         load_or_zero<T, VEC>(pg.z, i0, n, full, z);
@@ -79,14 +78,30 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) tc[j] = T(0);
         }
+        // each particle from its fields to its firing decision in one go: the
+        // fields of one particle are live at a time
+        const T cut = sg.proc == QED_PROC_QS ? cut_qs : cut_bw;
+        bool fire[VEC];
+        T chi[VEC];
+        int cnt = 0;
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-            wave_fields<T>(wt, x[j], ex[j], ey[j], ez[j], bx[j], by[j], bz[j]);
-            T vx, vy, vz;
-            boris_move<T>(pg.q, dt, ex[j], ey[j], ez[j], bx[j], by[j], bz[j], px[j], py[j], pz[j], vx, vy, vz);
+            T ex, ey, ez, bx, by, bz, vx, vy, vz;
+            wave_fields<T>(wt, x[j], ex, ey, ez, bx, by, bz);
+            boris_move<T>(pg.q, dt, ex, ey, ez, bx, by, bz, px[j], py[j], pz[j], vx, vy, vz);
             x[j] = x[j] + vx * dt;
             y[j] = y[j] + vy * dt;
             z[j] = z[j] + vz * dt;
+            if (store_fields && i0 + j < n) {
+                pg.ex[i0 + j] = ex, pg.ey[i0 + j] = ey, pg.ez[i0 + j] = ez;
+                pg.bx[i0 + j] = bx, pg.by[i0 + j] = by, pg.bz[i0 + j] = bz;
+            }
+            T c = tc[j];
+            fire[j] = evolve_one<T>(sg.proc, s_qs, s_bw, tab, px[j], py[j], pz[j], ex, ey, ez, bx, by, bz, dt, cut,
+                                    tau[j], c, chi[j], bad);
+            tc[j] = c;
+            fire[j] = fire[j] && (i0 + j < n);
+            cnt += fire[j] ? 1 : 0;
         }
         store_live<T, VEC>(pg.x, i0, n, full, x);
         store_live<T, VEC>(pg.y, i0, n, full, y);
@@ -96,16 +111,9 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
             store_live<T, VEC>(pg.py, i0, n, full, py);
             store_live<T, VEC>(pg.pz, i0, n, full, pz);
         }
-        if (store_fields) {
-            store_live<T, VEC>(pg.ex, i0, n, full, ex);
-            store_live<T, VEC>(pg.ey, i0, n, full, ey);
-            store_live<T, VEC>(pg.ez, i0, n, full, ez);
-            store_live<T, VEC>(pg.bx, i0, n, full, bx);
-            store_live<T, VEC>(pg.by, i0, n, full, by);
-            store_live<T, VEC>(pg.bz, i0, n, full, bz);
-        }
-        evolve_regs<T, VEC>(sg, n, i0, full, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt,
-                            sg.proc == QED_PROC_QS ? cut_qs : cut_bw, stats, 0, bad);
+        store_live<T, VEC>(sg.tau, i0, n, full, tau);
+        if constexpr (sizeof(T) == 4) store_live<T, VEC>(sg.tau_c, i0, n, full, tc);
+        compact_fire<T, VEC>(sg, i0, fire, chi, cnt, stats);
     }
     if (stats) warp_count(stats + QED_STAT_NONFINITE, bad);
 }

@@ -1,13 +1,14 @@
 // mlp.cu -- the learned sampler's object, training (forward + backward on the
 // CUDA cores in FP32 with the same bf16 rounding as inference, Adam), batch
-// inference on the tensor cores, and batch sampling through the 2-D tables for
-// comparison.
+// inference with the 64x64 layer on the tcgen05 tensor cores, and batch
+// sampling through the 2-D tables for comparison.
 #include <cmath>
 #include <cstring>
 
 #include "launch.cuh"
 #include "mlp.cuh"
 #include "physics.cuh"
+#include "tcgen05.cuh"
 
 namespace qed {
 
@@ -195,26 +196,143 @@ __global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfl
 }
 
 // ---------------------------------------------------------------------------
-// batch inference on the tensor cores: each warp evaluates 32 samples
+// batch inference with the 64x64 layer on the fifth-generation tensor cores.
+// A CTA of 256 threads is two independent groups of 128 (four warps each); a
+// group takes a tile of 128 samples per round: thread t of the group evaluates
+// layer 1 of its sample into row t of the group's A operand (bf16, core-matrix
+// layout); one thread issues four K = 16 MMAs of M = 128, N = 64 into the
+// group's FP32 accumulator in tensor memory and commits them to the group's
+// mbarrier; then every thread reads the 64 accumulators of its own row (its TMEM
+// lane) back for bias, GELU and layer 3.  The groups synchronise only among
+// themselves (named barriers), so one group's layer 1 overlaps the other's MMA.
+// (The event kernels evaluate the network 32 samples per warp inside their own
+// loops and keep the warp-level mma.sync form of mlp_forward_warp.)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kInferThreads) mlp_sample_kernel(MlpView v, const double *__restrict__ chi,
+constexpr int kTcThreads = 256;
+constexpr int kTcTile = 128;
+constexpr uint32_t kTcCols = 2 * kMlpH;  // one FP32 accumulator of N = 64 columns per group
+
+struct TcSmem {
+    __nv_bfloat16 b[kMlpH * kMlpH];       // W2 [n][k] (B operand, K-major)
+    __nv_bfloat16 a[2][kTcTile * kMlpH];  // H1 of each group's tile [m][k] (A operand, K-major)
+    float w1[kMlpH * 2], b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    float b3;
+    alignas(8) uint64_t bar[2];
+    uint32_t tmem;
+    int fail[2];
+};
+// Dynamic shared memory per CTA, padded so that at most four CTAs share an SM:
+// four times kTcCols is the SM's 512 TMEM columns, so no allocation waits.
+constexpr int kTcSmemBytes = 48 * 1024;
+static_assert(sizeof(TcSmem) <= kTcSmemBytes, "shared memory of the tensor-core sampler");
+
+__device__ __forceinline__ void group_sync(int group)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kTcTile) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
                                                                      const double *__restrict__ uu, int64_t n,
                                                                      double *__restrict__ xi)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);
-    mlp_stage(S.net, v.w);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, grp = tid / kTcTile, row = tid % kTcTile;
+    for (int i = tid; i < kMlpH * kMlpH; i += kTcThreads)
+        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(S.b) + core_offset(i / kMlpH, i % kMlpH)) =
+            v.w[kOffW2 + i];
+    for (int i = tid; i < kMlpH * 2; i += kTcThreads) S.w1[i] = __bfloat162float(v.w[kOffW1 + i]);
+    for (int i = tid; i < kMlpH; i += kTcThreads) {
+        S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
+        S.b2[i] = __bfloat162float(v.w[kOffB2 + i]);
+        S.w3[i] = __bfloat162float(v.w[kOffW3 + i]);
+    }
+    if (tid == 0) {
+        S.b3 = __bfloat162float(v.w[kOffB3]);
+        S.fail[0] = S.fail[1] = 0;
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(&S.tmem, kTcCols);
+    fence_async_smem();  // W2 was written by ordinary stores and is read by the tensor core
+    tc_fence_before();
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * kInferWarps + warp, nw = (int64_t)gridDim.x * kInferWarps;
-    for (int64_t base = gw * 32; base < n; base += nw * 32) {
-        const int64_t i = base + lane;
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    constexpr uint32_t idesc = idesc_bf16_f32(kTcTile, kMlpH);
+    const uint64_t bdesc = smem_desc(smem_u32(S.b), 128, 1024);
+    const uint64_t adesc = smem_desc(smem_u32(S.a[grp]), 128, 1024);
+    const uint32_t dacc = tmem + (uint32_t)(grp * kMlpH);  // the group's accumulator (lane 0)
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[grp]) + core_offset(row, 0);
+    // this thread's row: TMEM lane 32 (warp % 4) + lane
+    const uint32_t tacc = dacc + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t parity = 0;
+    const int64_t stride = (int64_t)gridDim.x * 2 * kTcTile;
+    for (int64_t base = ((int64_t)blockIdx.x * 2 + grp) * kTcTile; base < n; base += stride) {
+        const int64_t i = base + row;
         const bool valid = i < n;
         const double c = valid ? chi[i] : 1.0, u = valid ? uu[i] : 0.5;
         float x1, x2;
         mlp_features(v, c, u, x1, x2);
-        const float y = mlp_forward_warp(S.net, S.h1[warp], S.y[warp], x1, x2);
+        // layer 1 on the CUDA cores, rounded to bf16 into row `row` of the A tile
+#pragma unroll
+        for (int kc = 0; kc < kMlpH / 8; ++kc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = kc * 8 + 2 * q;
+                const float a = gelu(fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k])));
+                const float b = gelu(fmaf(S.w1[2 * k + 2], x1, fmaf(S.w1[2 * k + 3], x2, S.b1[k + 1])));
+                w[q] = pack_bf16(a, b);
+            }
+            *reinterpret_cast<uint4 *>(arow + kc * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        fence_async_smem();
+        tc_fence_before();  // (orders the previous round's accumulator loads before the barrier)
+        group_sync(grp);
+        if (S.fail[grp]) {  // an earlier wait of this group gave up (never expected): stop
+            for (int64_t b = base; b < n; b += stride)
+                if (b + row < n) xi[b + row] = __longlong_as_double(0x7ff8000000000000LL);
+            break;
+        }
+        if (row == 0) {
+            tc_fence_after();
+            // layer 2: Z = H1 W2^T, K = 64 in four steps of 16 (two core matrices, 256 bytes)
+#pragma unroll
+            for (int kk = 0; kk < kMlpH / 16; ++kk) {
+                const uint64_t step = (uint64_t)(kk * 256 >> 4);
+                tc_mma_bf16(dacc, adesc + step, bdesc + step, idesc, kk > 0);
+            }
+            tc_commit(&S.bar[grp]);
+        }
+        const bool done = mbar_wait(&S.bar[grp], parity);
+        parity ^= 1u;
+        if (!done) {
+            S.fail[grp] = 1;  // seen by the whole group after its next barrier
+            if (valid) xi[i] = __longlong_as_double(0x7ff8000000000000LL);
+            continue;
+        }
+        tc_fence_after();
+        // bias, GELU and layer 3 on this thread's 64 accumulators
+        float y = S.b3;
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+            uint32_t r[16];
+            tc_ld16(tacc + (uint32_t)c0, r);
+            tc_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) y = fmaf(S.w3[c0 + j], gelu(__uint_as_float(r[j]) + S.b2[c0 + j]), y);
+        }
         if (valid) xi[i] = mlp_output(v.proc, y, u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (S.fail[grp]) mbar_wait(&S.bar[grp], parity ^ 1u);  // one more bounded wait for the MMAs in flight
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_free(tmem, kTcCols);
     }
 }
 
@@ -406,13 +524,19 @@ extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const d
     if ((s = check_batch(d_chi, d_u, d_xi, n, true))) return s;
     if (n == 0) return QED_OK;
     static bool attr = false;
-    const size_t sm = sizeof(InferSmem);
     if (!attr) {
-        QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        // the largest shared-memory carveout, so that four CTAs (48 KB each) fit on an SM
+        QED_CUDA_TRY(
+            cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes));
+        QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
         attr = true;
     }
-    const int blocks = resident_grid<mlp_sample_kernel>(kInferThreads, sm, n);
-    mlp_sample_kernel<<<blocks, kInferThreads, sm, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n, d_xi);
+    // four CTAs per SM (the TMEM budget; more never become resident), fewer for small batches
+    const int64_t want = (n + 2 * kTcTile - 1) / (2 * kTcTile), cap = (int64_t)sm_count() * 4;
+    const int blocks = (int)(want < cap ? want : cap);
+    mlp_sample_tc_kernel<<<blocks, kTcThreads, kTcSmemBytes, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n,
+                                                                                 d_xi);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }

@@ -14,6 +14,14 @@ __device__ __forceinline__ double d_exp(double x) { return exp(x); }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float d_fma(float a, float b, float c) { return fmaf(a, b, c); }
+// logarithm and exponential of the 1-D rate lookups: in FP32 the hardware's
+// approximate forms (__logf: absolute error ~2^-21 near 1; __expf: ~2 + 1.2 |x|
+// ulp), whose ~1e-6 relative effect on a rate is far below the tables'
+// interpolation error; FP64 keeps the library functions
+__device__ __forceinline__ float r_log(float x) { return __logf(x); }
+__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ float r_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
 __device__ __forceinline__ double d_fma(double a, double b, double c) { return fma(a, b, c); }
 
 // leading asymptotes of T outside the table (Eq. (t_func), read in the paper's
@@ -33,18 +41,19 @@ constexpr double kLnTLarge = -0.9686047877362934;  // ln kTLarge
 // chi = |E|.  FP64 keeps the difference form: its cancellation error, 1e-16
 // (S/chi)^2 relative, is below the FP64 tolerance, and it saves the FP64
 // square root and division of n, FP64 being GB300's scarce unit.
-// gamma, 1/gamma, |p| and 1/|p| come from reciprocal square roots (rsqrtf within
-// 2 ulp, FP64 rsqrt within 1 ulp): the rate then multiplies instead of dividing,
-// and no IEEE division or square root but the last one of chi is left.
+// The rate multiplies by 1/gamma.  FP64 takes gamma and 1/gamma from one
+// reciprocal square root (within 1 ulp); FP32 keeps IEEE square roots and
+// divisions here (with reciprocal square roots the HBM-bound evolution kernel
+// measured ~1.5 % slower; photons, below, take them).
 // Returns chi, gamma and 1/gamma; NaN inputs give NaN.
 __device__ __forceinline__ float chi_lepton(float px, float py, float pz, float ex, float ey, float ez, float bx,
                                             float by, float bz, float &gamma, float &inv_gamma)
 {
     const float p2 = px * px + py * py + pz * pz;
-    const float g2 = 1.0f + p2;
-    inv_gamma = rsqrtf(g2);
-    gamma = g2 * inv_gamma;
-    const float inv = p2 > 0.0f ? rsqrtf(p2) : 0.0f;
+    gamma = sqrtf(1.0f + p2);
+    inv_gamma = 1.0f / gamma;
+    const float pm = sqrtf(p2);
+    const float inv = pm > 0.0f ? 1.0f / pm : 0.0f;
     const float nx = px * inv, ny = py * inv, nz = pz * inv;
     const float ne = nx * ex + ny * ey + nz * ez;
     const float fx = gamma * (ex - ne * nx) + (py * bz - pz * by);
@@ -70,7 +79,8 @@ __device__ __forceinline__ double chi_lepton(double px, double py, double pz, do
 
 // chi_gamma of a photon, §2 (gamma -> |p|, v -> c n).  FP32: | |p| E_perp + p x B |,
 // the perpendicular part of |p| E + p x B; FP64: the difference form.  Returns
-// chi, |p| and 1/|p| (0 for p = 0), from a reciprocal square root.
+// chi, |p| and 1/|p| (0 for p = 0), from a reciprocal square root (rsqrtf within
+// 2 ulp, FP64 rsqrt within 1 ulp).
 __device__ __forceinline__ float chi_photon(float px, float py, float pz, float ex, float ey, float ez, float bx,
                                             float by, float bz, float &pm, float &inv_pm)
 {
@@ -120,8 +130,8 @@ template <typename T>
 __device__ __forceinline__ T qs_rate(const T *tab, const Table1D<T> &v, T chi, T, T inv_gamma)
 {
     if (!(chi > T(0))) return T(0);
-    const T lnG = interp_ln(tab, d_log(chi), v.ln_min, v.inv_d, v.n);
-    return T(2.0 / 3.0 * kAlpha) * d_exp(lnG) * inv_gamma;
+    const T lnG = interp_ln(tab, r_log(chi), v.ln_min, v.inv_d, v.n);
+    return T(2.0 / 3.0 * kAlpha) * r_exp(lnG) * inv_gamma;
 }
 
 // BW rate (Eq. (bw_cross_tot)): alpha chi T(chi) / gamma_g; the asymptotes of
@@ -132,7 +142,7 @@ template <typename T>
 __device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T pm, T inv_pm)
 {
     if (!(chi > T(0)) || !(pm > T(0))) return T(0);
-    const T lc = d_log(chi);
+    const T lc = r_log(chi);
     T lnT;
     if (chi < v.chi_min)
         lnT = T(kLnTSmall) - T(8.0 / 3.0) / chi;
@@ -140,7 +150,7 @@ __device__ __forceinline__ T bw_rate(const T *tab, const Table1D<T> &v, T chi, T
         lnT = d_fma(lc, T(-1.0 / 3.0), T(kLnTLarge));
     else
         lnT = interp_ln(tab, lc, v.ln_min, v.inv_d, v.n);
-    return T(kAlpha) * chi * d_exp(lnT) * inv_pm;
+    return T(kAlpha) * chi * r_exp(lnT) * inv_pm;
 }
 
 // uniform for sampling in the working precision: FP64 as drawn; FP32 rounded

@@ -62,6 +62,34 @@ def test_forward_matches_oracle(api, tables, proc):
     assert np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
 
 
+def _forward_error(api, tables, m, proc, chi, u):
+    theta = m.get_params(proc).astype(np.float64)
+    xi = m.sample(proc, torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
+    cmin, cmax = _ranges(api, tables, proc)
+    y_ref, _ = omlp.forward(theta, omlp.features(proc, chi, u, cmin, cmax), round_bf16=True)
+    if proc == 0:
+        y_gpu, ok = np.log(xi) - 3 * np.log(u), y_ref + 3 * np.log(u) < -1e-3
+    else:
+        y_gpu, ok = np.where(u <= 0.5, xi, 1 - xi), (y_ref > 1e-3) & (y_ref < 0.5 - 1e-3)
+    return xi, np.abs(y_gpu[ok] - y_ref[ok])
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 256, 257, 300_001])
+def test_tensor_core_tiles_and_ragged_sizes(api, tables, n):
+    """The tcgen05 inference kernel takes 2 x 128 samples per CTA round (one
+    TMEM lane per sample): partial tiles, one sample, and many rounds per CTA
+    against the FP64 network; the same inputs give the same bits twice."""
+    proc = n % 2
+    m = api.Mlp(tables, seed=41 + proc)
+    chi, u = _batch(api, tables, proc, n, 50 + n)
+    xi, d = _forward_error(api, tables, m, proc, chi, u)
+    assert np.all(np.isfinite(xi))
+    if len(d):
+        assert np.max(d) < 2e-2 and np.median(d) < 2e-3, (np.median(d), np.max(d))
+    xi2 = m.sample(proc, torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.array_equal(xi, xi2)
+
+
 @pytest.mark.parametrize("proc", [0, 1])
 def test_gradients_match_oracle(api, tables, proc):
     m = api.Mlp(tables, seed=11 + proc)
