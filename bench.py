@@ -104,8 +104,8 @@ def profile_record(name: str, key: str):
 
 
 def traffic_record():
-    """DRAM bytes per particle of the FP32 evolution kernel."""
-    return profile_record("evolve_kernel_fp32_traffic.txt", "dram_bytes_per_particle")
+    """DRAM bytes per particle of the FP32 evolution kernel (the bulk-copy pipeline)."""
+    return profile_record("evolve_bulk_kernel_fp32_traffic.txt", "dram_bytes_per_particle")
 
 
 # FP64 pipe of GB300: 2 thread instructions per SM per clock (profiles/evolve_kernel_fp64_pipe.md)
@@ -479,7 +479,7 @@ def gpu_main(args):
     hbm, which = peaks()
     ach = BYTES_F32 * r["n_before"] / (ev_mean * 1e-3) / 1e9
     traffic_bpp = traffic_record()
-    roofline = {"bound": "hbm", "kernel": "evolve_kernel<float,4,4,4>", "achieved": round(ach, 1), "peak": hbm,
+    roofline = {"bound": "hbm", "kernel": "evolve_bulk_kernel<16,2,1,4>", "achieved": round(ach, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_kind": which,
                 "traffic": (traffic_bpp * r["n_before"]) if traffic_bpp else None,
                 "algorithmic_bytes": BYTES_F32 * r["n_before"], "evolve_ms": round(ev_mean, 4),
