@@ -151,9 +151,9 @@ typedef struct {
  * the default (8 consumer warps, 4 stages, 1 CTA per SM).  DIRECT in FP32
  * runs 4 CTAs of 256 threads per SM (64 registers), or 3 (80 registers) with
  * evolve_ctas_per_sm 3.  All give identical results.  DEFAULT (with
- * evolve_threads and evolve_ctas_per_sm 0) is BULK with 16 consumer warps and
- * 2 stages in FP32 when the arrays are 16-byte aligned, the fastest on GB300,
- * and DIRECT otherwise. */
+ * evolve_threads and evolve_ctas_per_sm 0) is a bulk-copy pipeline with 15
+ * consumer warps and 2 stages in FP32 when the arrays are 16-byte aligned, the
+ * fastest on GB300, and DIRECT otherwise. */
 enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 
 /* ------------------------------------------------------------------------- */

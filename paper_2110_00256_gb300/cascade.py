@@ -3,8 +3,8 @@ counter-propagating a linearly polarised plane wave whose fields are evaluated
 analytically at each particle, the substep (photon emission, pair production)
 after every push, all steps captured in one CUDA graph with a device step
 counter.  By default the push is fused into the evolution
-(qed_push_substep_batched: one pass per particle, 5 launches per step);
-fused=False runs the separate push and substep (6 launches per step) with the
+(qed_push_substep_batched: one pass per particle, 4 launches per step);
+fused=False runs the separate push and substep (5 launches per step) with the
 evolution launch shape chosen by qed_tune_evolve.
 
 Parameters: 64 patches with round(10^(3 + 4U)) electrons each (seed 7), gamma =
@@ -107,5 +107,5 @@ def run(tables: api.Tables, steps: int = 2000, scale: float = 1.0, photon_factor
     particle_steps = s["evolved"]
     return {"patches": int(len(counts)), "electrons": int(counts.sum()), "steps": steps, "ms": ms,
             "particle_steps": particle_steps, "value": particle_steps / (ms * 1e-3), "n_start": n0, "n_end": n1,
-            "graph_nodes_per_step": 5 if fused else 6, "capture_s": capture_s, "tuned": tuned, "stats": s,
-            "launches_per_step": 5 if fused else 6, "fused": fused}
+            "graph_nodes_per_step": 4 if fused else 5, "capture_s": capture_s, "tuned": tuned, "stats": s,
+            "launches_per_step": 4 if fused else 5, "fused": fused}

@@ -1,8 +1,9 @@
 // batched.cu -- the substep over many patches (each with its own electrons,
-// positrons and photons of uneven size) in five launches per step, whatever
+// positrons and photons of uneven size) in four launches per step, whatever
 // the number of patches: zero the firing counts, one evolution launch over all
-// 3 x n segments, one pair-production launch over all photon firing lists, one
-// photon-emission launch over all lepton firing lists, one clamp.  The segment
+// 3 x n segments, one event launch over all firing lists (photon emission of
+// the leptons, pair production of the photons; with the learned sampler, one
+// launch per process), one clamp.  The segment
 // descriptors live in device memory owned by a qed_batch (made once), so the
 // step allocates nothing and can be captured in a CUDA graph; with
 // opts->d_step a captured step replays as many steps.  qed_tune_evolve picks
@@ -82,15 +83,18 @@ __global__ void clamp_batch_kernel(const ClampEntry *e, int n, int64_t *step)
 }
 
 // Block-wide prefix of the 32-entry chunk counts of n_seg firing lists into
-// s_end (inclusive); s_n receives the clamped list lengths.
+// s_end (inclusive); s_n receives the clamped list lengths.  The lists are
+// a[0 .. na) followed by b[0 .. n_seg - na).
 template <typename T>
-__device__ void chunk_prefix(const EventSeg<T> *segs, int n_seg, long long *s_end, long long *s_n, long long *s_warp)
+__device__ void chunk_prefix(const EventSeg<T> *a, int na, const EventSeg<T> *b, int n_seg, long long *s_end,
+                             long long *s_n, long long *s_warp)
 {
     const int per = (n_seg + blockDim.x - 1) / blockDim.x;
     const int s0 = threadIdx.x * per, s1 = min(n_seg, s0 + per);
     long long local = 0;
     for (int s = s0; s < s1; ++s) {
-        const long long n = fire_n(segs[s].fire_count, segs[s].fire_cap);
+        const EventSeg<T> &g = s < na ? a[s] : b[s - na];
+        const long long n = fire_n(g.fire_count, g.fire_cap);
         s_n[s] = n;
         local += (n + 31) / 32;
     }
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(256, (MLP || sizeof(T) == 8) ? 1 : 4)
     long long *s_end = reinterpret_cast<long long *>(smem_raw + (MLP ? sizeof(InferSmem) : 0));
     long long *s_n = s_end + n_seg;
     if constexpr (MLP) mlp_stage(S.net, c.mlpv.w);
-    chunk_prefix<T>(segs, n_seg, s_end, s_n, s_warp);
+    chunk_prefix<T>(segs, n_seg, segs, n_seg, s_end, s_n, s_warp);
     const long long total = s_end[n_seg - 1];
     const int64_t step = event_step(c.d_step, c.step);
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -151,6 +155,40 @@ __global__ void __launch_bounds__(256, (MLP || sizeof(T) == 8) ? 1 : 4)
             bw_event_chunk<T, MLP>(segs[s], c, step, base, s_n[s], S, k);
     }
     flush_counts(c.stats, k, QS);
+}
+
+// Both processes in one launch (table sampler): the photon emission of every
+// lepton list and the pair production of every photon list touch disjoint
+// particles (see events3_kernel), so their chunks run side by side.
+// Dynamic shared memory: [s_end n][s_n n], n = n_qs + n_bw.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4)
+    event_batched_all_kernel(const EventSeg<T> *__restrict__ qs, int n_qs, const EventSeg<T> *__restrict__ bw,
+                             int n_bw, const __grid_constant__ EventCommon<T> cq,
+                             const __grid_constant__ EventCommon<T> cb)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_warp[8];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);  // (not touched without the learned sampler)
+    const int n_seg = n_qs + n_bw;
+    long long *s_end = reinterpret_cast<long long *>(smem_raw);
+    long long *s_n = s_end + n_seg;
+    chunk_prefix<T>(qs, n_qs, bw, n_seg, s_end, s_n, s_warp);
+    const long long total = s_end[n_seg - 1];
+    const int64_t step = event_step(cq.d_step, cq.step);
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    EventCounts kq, kb;
+    for (long long ch = warp; ch < total; ch += nwarp) {
+        const int s = find_seg(s_end, n_seg, ch);
+        const int64_t base = (ch - (s ? s_end[s - 1] : 0)) * 32;
+        if (s < n_qs)
+            qs_event_chunk<T, false>(qs[s], cq, step, base, s_n[s], S, kq);
+        else
+            bw_event_chunk<T, false>(bw[s - n_qs], cb, step, base, s_n[s], S, kb);
+    }
+    flush_counts(cq.stats, kq, true);
+    flush_counts(cb.stats, kb, false);
 }
 
 // CTAs of 256 threads for `warps` warp chunks of work, at most the resident count
@@ -193,6 +231,28 @@ static qed_status launch_events_batched(const qed_batch *b, const EventCommon<T>
         }
         k<<<resident_grid(warps, per_sm), 256, dyn, st>>>(segs, n_seg, c);
     }
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
+template <typename T>
+static qed_status launch_events_batched_all(const qed_batch *b, const EventCommon<T> &cq, const EventCommon<T> &cb,
+                                           cudaStream_t st)
+{
+    const int n_qs = 2 * b->n_patches, n_bw = b->n_patches;
+    const size_t dyn = (size_t)(n_qs + n_bw) * 2 * sizeof(long long);
+    const int64_t warps = (b->fire_capacity_max * 3 + 31) / 32;
+    constexpr int kMaxDyn = 3 * QED_MAX_PATCHES * 2 * (int)sizeof(long long);
+    auto k = event_batched_all_kernel<T>;
+    static bool attr = false;
+    static int per_sm = 0;
+    if (!attr) {
+        QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+        QED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, kMaxDyn));
+        attr = true;
+    }
+    k<<<resident_grid(warps, per_sm), 256, dyn, st>>>((const EventSeg<T> *)b->d_qs, n_qs,
+                                                      (const EventSeg<T> *)b->d_bw, n_bw, cq, cb);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
@@ -295,8 +355,15 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
     if (s) return s;
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
     const bool mlp = o && o->sampler == 1;
-    if ((s = launch_events_batched<T, false>(b, event_common<T>(t, QED_PROC_BW, seed, step, o), mlp, st))) return s;
-    if ((s = launch_events_batched<T, true>(b, event_common<T>(t, QED_PROC_QS, seed, step, o), mlp, st))) return s;
+    if (mlp) {
+        if ((s = launch_events_batched<T, false>(b, event_common<T>(t, QED_PROC_BW, seed, step, o), true, st)))
+            return s;
+        if ((s = launch_events_batched<T, true>(b, event_common<T>(t, QED_PROC_QS, seed, step, o), true, st)))
+            return s;
+    } else if ((s = launch_events_batched_all<T>(b, event_common<T>(t, QED_PROC_QS, seed, step, o),
+                                                   event_common<T>(t, QED_PROC_BW, seed, step, o), st))) {
+        return s;
+    }
     clamp_batch_kernel<<<(6 * n + 255) / 256, 256, 0, st>>>(b->d_clamp, 6 * n, o ? o->d_step : nullptr);
     QED_LAUNCH_CHECK();
     return QED_OK;

@@ -1,6 +1,7 @@
 // events.cu -- the event kernels of the substep for one firing list each:
 // quantum-synchrotron photon emission (§2.2, §3.2) and Breit-Wheeler pair
-// production (§2.1, §3.1), and the fused three-species substep entry point.
+// production (§2.1, §3.1), one kernel for the three lists of a substep, and the
+// fused three-species substep entry point.
 // The per-warp routines are in events.cuh (shared with the batched kernels).
 #include "events.cuh"
 #include "evolve.cuh"
@@ -49,6 +50,45 @@ __global__ void __launch_bounds__(256) bw_event_kernel(const __grid_constant__ E
     for (int64_t base = warp * 32; base < nf; base += nwarp * 32)
         bw_event_chunk<T, MLP>(a.seg, a.com, step, base, nf, S, k);
     flush_counts(a.com.stats, k, false);
+}
+
+// The three firing lists of one substep in one launch (table sampler):
+// photon emission of the electrons and of the positrons, pair production of
+// the photons.  They touch disjoint particles (each reads and updates its own
+// parents below the pre-step counts and appends to another species), so their
+// chunks of 32 entries run side by side; the chunk index runs over the three
+// lists one after the other.
+template <typename T>
+struct Events3Args {
+    EventSeg<T> seg[3];  // electrons -> photons, positrons -> photons, photons -> pairs
+    EventCommon<T> qs, bw;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) events3_kernel(const __grid_constant__ Events3Args<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InferSmem &S = *reinterpret_cast<InferSmem *>(smem_raw);  // (not touched without the learned sampler)
+    int64_t nf[3], c1, c2, c3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) nf[k] = fire_n(a.seg[k].fire_count, a.seg[k].fire_cap);
+    c1 = (nf[0] + 31) / 32;
+    c2 = c1 + (nf[1] + 31) / 32;
+    c3 = c2 + (nf[2] + 31) / 32;
+    const int64_t step = event_step(a.qs.d_step, a.qs.step);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    EventCounts kq, kb;
+    for (int64_t c = warp; c < c3; c += nwarp) {
+        if (c < c1)
+            qs_event_chunk<T, false>(a.seg[0], a.qs, step, c * 32, nf[0], S, kq);
+        else if (c < c2)
+            qs_event_chunk<T, false>(a.seg[1], a.qs, step, (c - c1) * 32, nf[1], S, kq);
+        else
+            bw_event_chunk<T, false>(a.seg[2], a.bw, step, (c - c2) * 32, nf[2], S, kb);
+    }
+    flush_counts(a.qs.stats, kq, true);
+    flush_counts(a.bw.stats, kb, false);
 }
 
 __global__ void zero3(int64_t *a, int64_t *b, int64_t *c)
@@ -229,9 +269,31 @@ static qed_status substep_impl(const qed_tables *t, const qed_species *e, const 
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
     // the event kernels clamp the firing counts on read and the species counts
     // after their appends
-    if ((s = launch_pairs<T>(t, g, e, p, &fire[2], seed, step, o, st, false))) return s;
-    if ((s = launch_photons<T>(t, e, g, &fire[0], seed, step, o, st, false))) return s;
-    if ((s = launch_photons<T>(t, p, g, &fire[1], seed, step, o, st, false))) return s;
+    if (o && o->sampler == 1) {
+        if ((s = launch_pairs<T>(t, g, e, p, &fire[2], seed, step, o, st, false))) return s;
+        if ((s = launch_photons<T>(t, e, g, &fire[0], seed, step, o, st, false))) return s;
+        if ((s = launch_photons<T>(t, p, g, &fire[1], seed, step, o, st, false))) return s;
+    } else {
+        Events3Args<T> ea;
+        memset(&ea, 0, sizeof(ea));
+        const qed_species *par[3] = {e, p, g};
+        for (int k = 0; k < 3; ++k) {
+            EventSeg<T> &sg = ea.seg[k];
+            sg.parent = ptrs<T>(par[k]);
+            sg.fire_idx = fire[k].idx;
+            sg.fire_chi = fire[k].chi;
+            sg.fire_count = fire[k].d_count;
+            sg.fire_cap = fire[k].capacity;
+        }
+        ea.seg[0].out0 = ea.seg[1].out0 = ptrs<T>(g);
+        ea.seg[2].out0 = ptrs<T>(e);
+        ea.seg[2].out1 = ptrs<T>(p);
+        ea.qs = event_common<T>(t, QED_PROC_QS, seed, step, o);
+        ea.bw = event_common<T>(t, QED_PROC_BW, seed, step, o);
+        const int g3 = event_grid<events3_kernel<T>>(0, fire[0].capacity + fire[1].capacity + fire[2].capacity);
+        events3_kernel<T><<<g3, 256, 0, st>>>(ea);
+        QED_LAUNCH_CHECK();
+    }
     clamp_all<<<1, 32, 0, st>>>(ptrs<T>(e).count, e->capacity, ptrs<T>(p).count, p->capacity, ptrs<T>(g).count,
                                 g->capacity, (unsigned long long *)fire[0].d_count, fire[0].capacity,
                                 (unsigned long long *)fire[1].d_count, fire[1].capacity,

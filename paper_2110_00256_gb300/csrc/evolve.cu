@@ -407,10 +407,13 @@ qed_status launch_evolve(const EvolveArgs<T, MAXSEG> &a, bool vec_ok, int64_t ca
     // the grid is sized from the capacities (counts live on the device); idle
     // CTAs exit after reading the counts
     if constexpr (sizeof(T) == 4) {
-        // the default: bulk copies, 16 consumer warps, 2 stages (the fastest measured on GB300)
+        // the default: bulk copies, 15 consumer warps + the producer (16 warps, 4 per
+        // scheduler), 2 stages of 1920-particle tiles: the fastest of 7 .. 18 consumer
+        // warps and 2 .. 4 stages measured on GB300
         const bool dflt = pipeline == QED_EVOLVE_DEFAULT && threads == 0 && ctas_per_sm == 0;
         if (vec_ok && (pipeline == QED_EVOLVE_BULK || dflt) && grid_override <= 0) {
-            if (threads == 512 || dflt) return launch_bulk<16, 2, 1, MAXSEG>(a, capacity_sum, st);
+            if (dflt) return launch_bulk<15, 2, 1, MAXSEG>(a, capacity_sum, st);
+            if (threads == 512) return launch_bulk<16, 2, 1, MAXSEG>(a, capacity_sum, st);
             if (ctas_per_sm == 2) return launch_bulk<8, 2, 2, MAXSEG>(a, capacity_sum, st);
             return launch_bulk<8, 4, 1, MAXSEG>(a, capacity_sum, st);
         }
