@@ -20,7 +20,9 @@ namespace qed {
 constexpr uint32_t kPoisson = 4u, kPairIds = 5u;
 constexpr double kPi = 3.141592653589793;
 
-__device__ __forceinline__ double schwinger_rate(double ex, double ey, double ez, double bx, double by, double bz)
+// the rate of Eq. (shw) in FP64 (out of line, like poisson_draw and make_pairs:
+// the rare paths stay out of the streaming loop's registers)
+__device__ __noinline__ double schwinger_rate(double ex, double ey, double ez, double bx, double by, double bz)
 {
     const double F = 0.5 * ((ex * ex + ey * ey + ez * ez) - (bx * bx + by * by + bz * bz));
     const double G = ex * bx + ey * by + ez * bz;
@@ -33,7 +35,7 @@ __device__ __forceinline__ double schwinger_rate(double ex, double ey, double ez
     return eps * (eps / kPi) * xcothx * exp(-kPi / eps) / (4.0 * kPi * kPi);
 }
 
-__device__ __forceinline__ long long poisson_draw(double lambda, uint64_t seed, uint64_t cell, int64_t step)
+__device__ __noinline__ long long poisson_draw(double lambda, uint64_t seed, uint64_t cell, int64_t step)
 {
     if (!(lambda > 0.0)) return 0;
     const U4 w = draw(seed, cell, step, kPoisson);
@@ -148,9 +150,46 @@ __device__ __forceinline__ void load_cells(const T *a, int64_t i0, int64_t n, bo
     for (int j = 0; j < VEC; ++j) v[j] = i0 + j < n ? a[i0 + j] : T(0);
 }
 
-// ln_scale = ln(dv dt / (weight 4 pi^2)), in FP32 (+inf when it overflows)
+// the pairs of a warp's cells (rare; every lane of the warp calls it): slots
+// reserved with one atomic per warp and species, then written
 template <typename T, int VEC>
-__global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
+__device__ __noinline__ void make_pairs(const long long (&k)[VEC], long long tot, int64_t c0, const CellsView<T> &c,
+                                        double weight, uint64_t seed, int64_t step, const PairDest<T> &e,
+                                        const PairDest<T> &p, long long &made, long long &dropped)
+{
+    const long long se = warp_reserve_n(e.count, tot);
+    const long long sp = warp_reserve_n(p.count, tot);
+    long long off = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        const int64_t cell = c0 + j;
+        // slots [se + off, se + off + k) and [sp + off, ...); only those below the
+        // capacities exist, so the loop ends with the last of them whatever k is
+        const long long be = se + off, bp = sp + off;
+        const long long room_e = e.cap - be > 0 ? e.cap - be : 0, room_p = p.cap - bp > 0 ? p.cap - bp : 0;
+        const long long both = room_e < room_p ? room_e : room_p, any = room_e > room_p ? room_e : room_p;
+        const long long n_made = k[j] < both ? k[j] : both, n_touch = k[j] < any ? k[j] : any;
+        for (long long i = 0; i < n_touch; ++i) {
+            if (i < n_made) {
+                const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)i);
+                const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
+                put<T>(e, be + i, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
+                put<T>(p, bp + i, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
+            } else {  // room in one species only: a placeholder there
+                if (i < room_e) put_dead<T>(e, be + i);
+                if (i < room_p) put_dead<T>(p, bp + i);
+            }
+        }
+        made += n_made;
+        dropped += k[j] - n_made;
+        off += k[j];
+    }
+}
+
+// ln_scale = ln(dv dt / (weight 4 pi^2)), in FP32 (+inf when it overflows).
+// 3 CTAs of 256 per SM (80 registers): faster than 4 (64 registers, spills).
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256, 3) schwinger_kernel(CellsView<T> c, double dv, double dt, double weight,
                                                             uint64_t seed, int64_t step, PairDest<T> e,
                                                             PairDest<T> p, long long *stats, int vec, float ln_scale)
 {
@@ -182,6 +221,19 @@ __global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, doubl
             const float fbx = (float)bx[j], fby = (float)by[j], fbz = (float)bz[j];
             const float e2 = fex * fex + fey * fey + fez * fez, b2 = fbx * fbx + fby * fby + fbz * fbz;
             const float g = fex * fbx + fey * fby + fez * fbz, f = 0.5f * (e2 - b2);
+            // First a cheaper, looser bound from reciprocal square roots (each
+            // within 2 ulp, widened by 1e-6) and ln x <= x - 1, which settles
+            // the cells of PIC-strength fields; q >= eps_up^2 below.  q <= 0 with
+            // finite fields means eps = 0: no pair.
+            const float s2 = e2 + b2, r2 = f * f + g * g;
+            const float q = (r2 > 0.0f ? r2 * rsqrtf(r2) * 1.000001f : 0.0f) + f + 1.0e-6f * s2;
+            if (!(q > 0.0f) && q == q && s2 == s2) continue;
+            {
+                const float rq = rsqrtf(q);
+                const float eps_hi = q * rq * 1.000001f, pi_over_lo = 3.1415925f * rq * 0.999999f;
+                const float s_hi = (s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f) * 1.000001f;
+                if (eps_hi * (s_hi + eps_hi) - 1.0f - pi_over_lo + ln_scale < -45.0f) continue;
+            }
             const float eps_up = sqrtf(sqrtf(f * f + g * g) + f + 1.0e-6f * (e2 + b2));
             const float ln_up = logf(eps_up * (sqrtf(e2 + b2) + eps_up)) - 3.14159274f / eps_up + ln_scale;
             if (!(ln_up < -45.0f)) {  // -55 ln 2 = -38.1
@@ -191,34 +243,8 @@ __global__ void __launch_bounds__(256, 4) schwinger_kernel(CellsView<T> c, doubl
             }
             tot += k[j];
         }
-        if (!__any_sync(0xffffffffu, tot > 0)) continue;
-        const long long se = warp_reserve_n(e.count, tot);
-        const long long sp = warp_reserve_n(p.count, tot);
-        long long off = 0;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            const int64_t cell = c0 + j;
-            // slots [se + off, se + off + k) and [sp + off, ...); only those below the
-            // capacities exist, so the loop ends with the last of them whatever k is
-            const long long be = se + off, bp = sp + off;
-            const long long room_e = e.cap - be > 0 ? e.cap - be : 0, room_p = p.cap - bp > 0 ? p.cap - bp : 0;
-            const long long both = room_e < room_p ? room_e : room_p, any = room_e > room_p ? room_e : room_p;
-            const long long n_made = k[j] < both ? k[j] : both, n_touch = k[j] < any ? k[j] : any;
-            for (long long i = 0; i < n_touch; ++i) {
-                if (i < n_made) {
-                    const U4 w = draw(seed, (uint64_t)cell, step, kPairIds + 256u * (uint32_t)i);
-                    const uint64_t ide = ((uint64_t)w.y << 32) | w.x, idp = ((uint64_t)w.w << 32) | w.z;
-                    put<T>(e, be + i, c, cell, (T)weight, ide, tau_draw(seed, ide, step, kTauInit));
-                    put<T>(p, bp + i, c, cell, (T)weight, idp, tau_draw(seed, idp, step, kTauInit));
-                } else {  // room in one species only: a placeholder there
-                    if (i < room_e) put_dead<T>(e, be + i);
-                    if (i < room_p) put_dead<T>(p, bp + i);
-                }
-            }
-            made += n_made;
-            dropped += k[j] - n_made;
-            off += k[j];
-        }
+        if (__any_sync(0xffffffffu, tot > 0))
+            make_pairs<T, VEC>(k, tot, c0, c, weight, seed, step, e, p, made, dropped);
     }
     if (stats) {
         warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
