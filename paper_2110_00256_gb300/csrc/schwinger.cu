@@ -14,6 +14,7 @@
 #include "launch.cuh"
 #include "common.cuh"
 #include "physics.cuh"
+#include "pipeline.cuh"
 
 namespace qed {
 
@@ -150,13 +151,57 @@ __device__ __forceinline__ void load_cells(const T *a, int64_t i0, int64_t n, bo
     for (int j = 0; j < VEC; ++j) v[j] = i0 + j < n ? a[i0 + j] : T(0);
 }
 
-// the pairs of a warp's cells (rare; every lane of the warp calls it): slots
-// reserved with one atomic per warp and species, then written
+// The Poisson number of pairs of one cell.
+template <typename T>
+__device__ __forceinline__ long long cell_pairs(T ex, T ey, T ez, T bx, T by, T bz, int64_t cell, double dv, double dt,
+                                                double weight, uint64_t seed, int64_t step, float ln_scale)
+{
+    // Cells whose mean is below 2^-55 draw no pair whatever U (the largest
+    // uniform is 1 - 2^-54, below exp(-mean)).  A FP32 upper bound of the mean
+    // skips them: eps_up >= eps (eps^2 = sqrt(F^2 + G^2) + F plus a bound on its
+    // rounding, 1e-6 (E^2 + B^2)), eta coth(pi eta/eps) <= eta + eps/pi with
+    // eta <= sqrt(E^2 + B^2), and a margin of e^7 against FP32 rounding
+    const float fex = (float)ex, fey = (float)ey, fez = (float)ez;
+    const float fbx = (float)bx, fby = (float)by, fbz = (float)bz;
+    const float e2 = fex * fex + fey * fey + fez * fez, b2 = fbx * fbx + fby * fby + fbz * fbz;
+    const float g = fex * fbx + fey * fby + fez * fbz, f = 0.5f * (e2 - b2);
+    // First a cheaper, looser bound from reciprocal square roots (each
+    // within 2 ulp, widened by 1e-6) and ln x <= x - 1, which settles
+    // the cells of PIC-strength fields; q >= eps_up^2 below.  q <= 0 with
+    // finite fields means eps = 0: no pair.
+    const float s2 = e2 + b2, r2 = f * f + g * g;
+    const float q = (r2 > 0.0f ? r2 * rsqrtf(r2) * 1.000001f : 0.0f) + f + 1.0e-6f * s2;
+    if (!(q > 0.0f) && q == q && s2 == s2) return 0;
+    {
+        const float rq = rsqrtf(q);
+        const float eps_hi = q * rq * 1.000001f, pi_over_lo = 3.1415925f * rq * 0.999999f;
+        const float s_hi = (s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f) * 1.000001f;
+        if (eps_hi * (s_hi + eps_hi) - 1.0f - pi_over_lo + ln_scale < -45.0f) return 0;
+    }
+    const float eps_up = sqrtf(sqrtf(f * f + g * g) + f + 1.0e-6f * (e2 + b2));
+    const float ln_up = logf(eps_up * (sqrtf(e2 + b2) + eps_up)) - 3.14159274f / eps_up + ln_scale;
+    if (ln_up < -45.0f) return 0;  // -55 ln 2 = -38.1
+    const double rate = schwinger_rate((double)ex, (double)ey, (double)ez, (double)bx, (double)by, (double)bz);
+    return poisson_draw(rate * dv * dt / weight, seed, (uint64_t)cell, step);
+}
+
+// the pairs of a warp's cells (rare; every lane of the warp calls it): the
+// counts again, slots reserved with one atomic per warp and species, the pairs
+// written.  The streaming loops keep no per-cell array alive for it.
 template <typename T, int VEC>
-__device__ __noinline__ void make_pairs(const long long (&k)[VEC], long long tot, int64_t c0, const CellsView<T> &c,
-                                        double weight, uint64_t seed, int64_t step, const PairDest<T> &e,
+__device__ __noinline__ void make_pairs(int64_t c0, const CellsView<T> &c, double dv, double dt, double weight,
+                                        uint64_t seed, int64_t step, float ln_scale, const PairDest<T> &e,
                                         const PairDest<T> &p, long long &made, long long &dropped)
 {
+    // the counts again, from the cells in global memory (the same draws: counter-based)
+    long long k[VEC], tot = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        k[j] = c0 + j < c.n ? cell_pairs<T>(c.ex[c0 + j], c.ey[c0 + j], c.ez[c0 + j], c.bx[c0 + j], c.by[c0 + j],
+                                            c.bz[c0 + j], c0 + j, dv, dt, weight, seed, step, ln_scale)
+                            : 0;
+        tot += k[j];
+    }
     const long long se = warp_reserve_n(e.count, tot);
     const long long sp = warp_reserve_n(p.count, tot);
     long long off = 0;
@@ -207,44 +252,131 @@ __global__ void __launch_bounds__(256, 3) schwinger_kernel(CellsView<T> c, doubl
         load_cells<T, VEC>(c.bx, c0, c.n, vec, bx);
         load_cells<T, VEC>(c.by, c0, c.n, vec, by);
         load_cells<T, VEC>(c.bz, c0, c.n, vec, bz);
-        long long k[VEC], tot = 0;
+        long long tot = 0;
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            k[j] = 0;
-            if (c0 + j >= c.n) continue;
-            // Cells whose mean is below 2^-55 draw no pair whatever U (the largest
-            // uniform is 1 - 2^-54, below exp(-mean)).  A FP32 upper bound of the mean
-            // skips them: eps_up >= eps (eps^2 = sqrt(F^2 + G^2) + F plus a bound on its
-            // rounding, 1e-6 (E^2 + B^2)), eta coth(pi eta/eps) <= eta + eps/pi with
-            // eta <= sqrt(E^2 + B^2), and a margin of e^7 against FP32 rounding
-            const float fex = (float)ex[j], fey = (float)ey[j], fez = (float)ez[j];
-            const float fbx = (float)bx[j], fby = (float)by[j], fbz = (float)bz[j];
-            const float e2 = fex * fex + fey * fey + fez * fez, b2 = fbx * fbx + fby * fby + fbz * fbz;
-            const float g = fex * fbx + fey * fby + fez * fbz, f = 0.5f * (e2 - b2);
-            // First a cheaper, looser bound from reciprocal square roots (each
-            // within 2 ulp, widened by 1e-6) and ln x <= x - 1, which settles
-            // the cells of PIC-strength fields; q >= eps_up^2 below.  q <= 0 with
-            // finite fields means eps = 0: no pair.
-            const float s2 = e2 + b2, r2 = f * f + g * g;
-            const float q = (r2 > 0.0f ? r2 * rsqrtf(r2) * 1.000001f : 0.0f) + f + 1.0e-6f * s2;
-            if (!(q > 0.0f) && q == q && s2 == s2) continue;
-            {
-                const float rq = rsqrtf(q);
-                const float eps_hi = q * rq * 1.000001f, pi_over_lo = 3.1415925f * rq * 0.999999f;
-                const float s_hi = (s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f) * 1.000001f;
-                if (eps_hi * (s_hi + eps_hi) - 1.0f - pi_over_lo + ln_scale < -45.0f) continue;
-            }
-            const float eps_up = sqrtf(sqrtf(f * f + g * g) + f + 1.0e-6f * (e2 + b2));
-            const float ln_up = logf(eps_up * (sqrtf(e2 + b2) + eps_up)) - 3.14159274f / eps_up + ln_scale;
-            if (!(ln_up < -45.0f)) {  // -55 ln 2 = -38.1
-                const double rate = schwinger_rate((double)ex[j], (double)ey[j], (double)ez[j], (double)bx[j],
-                                                   (double)by[j], (double)bz[j]);
-                k[j] = poisson_draw(rate * dv * dt / weight, seed, (uint64_t)(c0 + j), step);
-            }
-            tot += k[j];
-        }
+        for (int j = 0; j < VEC; ++j)
+            if (c0 + j < c.n)
+                tot += cell_pairs<T>(ex[j], ey[j], ez[j], bx[j], by[j], bz[j], c0 + j, dv, dt, weight, seed, step,
+                                     ln_scale);
         if (__any_sync(0xffffffffu, tot > 0))
-            make_pairs<T, VEC>(k, tot, c0, c, weight, seed, step, e, p, made, dropped);
+            make_pairs<T, VEC>(c0, c, dv, dt, weight, seed, step, ln_scale, e, p, made, dropped);
+    }
+    if (stats) {
+        warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
+        warp_count64(stats + QED_STAT_DROPPED_CAPACITY, dropped);
+    }
+}
+
+// FP32 cells with 16-byte-aligned field arrays: the bulk-copy form.  The last
+// warp of the CTA copies whole tiles (TP = CW x 32 x 4 cells) of the six field
+// components into S shared-memory stages with cp.async.bulk (completion counted
+// on the stage's mbarrier); the CW consumer warps take four cells each from the
+// stage, release it, and settle the cells.  The ragged last tile is read from
+// global memory.  Every wait is bounded; a warp that gives up raises s_abort,
+// and QED_STAT_WAIT_TIMEOUT counts the CTA.
+constexpr int kCellArrays = 6;
+
+__device__ __forceinline__ bool cell_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort || clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cell_give_up(int *abort, long long *stats)
+{
+    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+}
+
+template <int CW, int S>
+__global__ void __launch_bounds__((CW + 1) * 32, 1)
+    schwinger_bulk_kernel(CellsView<float> c, double dv, double dt, double weight, uint64_t seed, int64_t step,
+                          PairDest<float> e, PairDest<float> p, long long *stats, float ln_scale)
+{
+    constexpr int TP = CW * 32 * 4;
+    extern __shared__ __align__(128) float s_stage[];  // [S][kCellArrays][TP]
+    __shared__ __align__(8) uint64_t s_full[S];
+    __shared__ __align__(8) uint64_t s_empty[S];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&s_full[k], 1);
+            mbar_init(&s_empty[k], CW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const long long total = (c.n + TP - 1) / TP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = &s_abort;
+    const float *arr[kCellArrays] = {c.ex, c.ey, c.ez, c.bx, c.by, c.bz};
+
+    if (warp == CW) {  // producer
+        const uint64_t pol = l2_evict_first();
+        int k = 0;
+        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+            const int st = k % S;
+            const uint32_t ph = (uint32_t)(k / S) & 1u;
+            const int64_t base = t * (int64_t)TP;
+            if (!__all_sync(0xffffffffu, cell_wait(&s_empty[st], ph ^ 1u, abort))) {
+                if (lane == 0) cell_give_up(&s_abort, stats);
+                break;
+            }
+            if (base + TP <= c.n) {
+                if (lane == 0) mbar_arrive_expect_tx(&s_full[st], kCellArrays * TP * (uint32_t)sizeof(float));
+                __syncwarp();
+                if (lane < kCellArrays)
+                    bulk_g2s(s_stage + ((size_t)st * kCellArrays + lane) * TP, arr[lane] + base,
+                             TP * (uint32_t)sizeof(float), &s_full[st], pol);
+            } else if (lane == 0) {
+                mbar_arrive(&s_full[st]);
+            }
+        }
+        // leave only once the copies of the last S tiles have landed
+        for (int j = 1; j <= S && j <= k; ++j) {
+            const int kk = k - j;
+            if (!mbar_wait(&s_full[kk % S], (uint32_t)(kk / S) & 1u) && lane == 0) cell_give_up(&s_abort, stats);
+        }
+        return;
+    }
+
+    long long made = 0, dropped = 0;
+    int k = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int st = k % S;
+        const uint32_t ph = (uint32_t)(k / S) & 1u;
+        const int64_t base = t * (int64_t)TP;
+        const int64_t c0 = base + 4 * (int64_t)threadIdx.x;
+        if (!__all_sync(0xffffffffu, cell_wait(&s_full[st], ph, abort))) {
+            if (lane == 0) cell_give_up(&s_abort, stats);
+            break;
+        }
+        float f[kCellArrays][4];
+        if (base + TP <= c.n) {
+            const float4 *v = reinterpret_cast<const float4 *>(s_stage + (size_t)st * kCellArrays * TP) + threadIdx.x;
+#pragma unroll
+            for (int a = 0; a < kCellArrays; ++a) {
+                const float4 w = v[a * (TP / 4)];
+                f[a][0] = w.x, f[a][1] = w.y, f[a][2] = w.z, f[a][3] = w.w;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < kCellArrays; ++a) load_cells<float, 4>(arr[a], c0, c.n, true, f[a]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[st]);
+        long long tot = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c0 + j < c.n)
+                tot += cell_pairs<float>(f[0][j], f[1][j], f[2][j], f[3][j], f[4][j], f[5][j], c0 + j, dv, dt, weight,
+                                         seed, step, ln_scale);
+        if (__any_sync(0xffffffffu, tot > 0))
+            make_pairs<float, 4>(c0, c, dv, dt, weight, seed, step, ln_scale, e, p, made, dropped);
     }
     if (stats) {
         warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
@@ -271,12 +403,35 @@ static qed_status launch(const qed_cells *cells, double dv, double dt, double we
     bool vec = true;
     for (const void *a : {cells->ex, cells->ey, cells->ez, cells->bx, cells->by, cells->bz})
         vec = vec && ((uintptr_t)a & 15u) == 0;
+    const double ln_scale = std::log(dv * dt / (weight * 4.0 * kPi * kPi));
+    const float ln_s = ln_scale < 1e30 ? (float)ln_scale : INFINITY;
+    if constexpr (sizeof(T) == 4) {
+        if (vec) {
+            // 15 consumer warps + the producer (16 warps per SM), 4 stages of 1920 cells
+            constexpr int CW = 15, S = 4;
+            constexpr int dyn = S * kCellArrays * CW * 32 * 4 * (int)sizeof(float);
+            static bool attr = false;
+            if (!attr) {
+                QED_CUDA_TRY(cudaFuncSetAttribute(schwinger_bulk_kernel<CW, S>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+                attr = true;
+            }
+            const int64_t tiles = (cells->n + CW * 128 - 1) / (CW * 128);
+            const int g = (int)(tiles < sm_count() ? tiles : sm_count());
+            schwinger_bulk_kernel<CW, S><<<g, (CW + 1) * 32, dyn, st>>>(c, dv, dt, weight, seed, step,
+                                                                        pair_dest<T>(el), pair_dest<T>(po),
+                                                                        (long long *)d_stats, ln_s);
+            QED_LAUNCH_CHECK();
+            clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
+                                                (unsigned long long *)po->d_count, po->capacity);
+            QED_LAUNCH_CHECK();
+            return QED_OK;
+        }
+    }
     constexpr int V = sizeof(T) == 4 ? 4 : 2;
     const int g = resident_grid<schwinger_kernel<T, V>>(256, 0, (cells->n + V - 1) / V);
-    const double ln_scale = std::log(dv * dt / (weight * 4.0 * kPi * kPi));
     schwinger_kernel<T, V><<<g, 256, 0, st>>>(c, dv, dt, weight, seed, step, pair_dest<T>(el), pair_dest<T>(po),
-                                              (long long *)d_stats, vec ? 1 : 0,
-                                              ln_scale < 1e30 ? (float)ln_scale : INFINITY);
+                                              (long long *)d_stats, vec ? 1 : 0, ln_s);
     QED_LAUNCH_CHECK();
     clamp_pair_counts<<<1, 32, 0, st>>>((unsigned long long *)el->d_count, el->capacity,
                                         (unsigned long long *)po->d_count, po->capacity);
