@@ -300,7 +300,9 @@ typedef struct {
  * optical depths from their ids; they are appended to `electrons` and
  * `positrons` (capacity-checked: a pair without room in both is not made and is
  * counted as dropped).  Rate and mean in FP64 at either precision.  d_stats:
- * QED_STAT_SCHWINGER_PAIRS and QED_STAT_DROPPED_CAPACITY, or NULL. */
+ * QED_STAT_SCHWINGER_PAIRS, QED_STAT_DROPPED_CAPACITY and (FP32 fields,
+ * 16-byte aligned: streamed through shared memory with bounded waits)
+ * QED_STAT_WAIT_TIMEOUT, or NULL. */
 qed_status qed_schwinger_pairs(const qed_cells *cells, double dv, double dt, double weight, uint64_t seed,
                                int64_t step, const qed_species *electrons,
                                const qed_species *positrons, qed_precision prec, int64_t *d_stats,
