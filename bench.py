@@ -304,9 +304,8 @@ E2E_OUT = ("px", "py", "pz", "tau", "tau_c")
 
 
 def e2e_host_buffers(capacity):
-    """Pinned host buffers of the end-to-end leg, made at the start of the run:
-    pinned in a fresh process, the copies took 25 ms per step against 35 ms
-    with the same buffers pinned after the other legs had run."""
+    """Pinned host buffers of the end-to-end leg, made once at the start of the
+    run (outside every timed region)."""
     import torch
     return {k: ({c: torch.empty(capacity, dtype=torch.float32, pin_memory=True) for c in E2E_IN},
                 {c: torch.empty(capacity, dtype=torch.float32, pin_memory=True) for c in E2E_OUT})

@@ -80,19 +80,23 @@ def test_schwinger_capacity_drops_whole_pairs(api):
     assert {pairs[i] for i in live_e} == live_p  # no half pairs
 
 
-def test_schwinger_weak_and_strong_field_mix(api):
+@pytest.mark.parametrize("prec_name", ["f64", "f32"])
+def test_schwinger_weak_and_strong_field_mix(api, prec_name):
     """cells around the FP64 underflow of exp(-pi/eps) (eps = 0.0042) and
     magnetic-dominated cells: the GPU skips only cells whose rate is exactly
-    zero, and counts equal the oracle's"""
+    zero (FP32: through both FP32 bounds of the streamed kernel), and counts
+    equal the oracle's"""
     r = np.random.default_rng(9)
     n = 30_000
+    dtype = np.float64 if prec_name == "f64" else np.float32
     scale = np.exp(r.uniform(np.log(1e-3), np.log(0.5), n))
-    f = {k: (r.normal(0, 1, n) * scale) for k in ("ex", "ey", "ez")}
-    f.update({k: (r.normal(0, 1, n) * scale * r.uniform(0, 30, n)) for k in ("bx", "by", "bz")})
-    pos = {k: np.zeros(n) for k in ("x", "y", "z")}
-    ref = oracle.schwinger(f, 500.0, 10.0, 1.0, 5, 1)
+    f = {k: (r.normal(0, 1, n) * scale).astype(dtype) for k in ("ex", "ey", "ez")}
+    f.update({k: (r.normal(0, 1, n) * scale * r.uniform(0, 30, n)).astype(dtype) for k in ("bx", "by", "bz")})
+    pos = {k: np.zeros(n, dtype=dtype) for k in ("x", "y", "z")}
+    ref = oracle.schwinger({k: v.astype(np.float64) for k, v in f.items()}, 500.0, 10.0, 1.0, 5, 1)
     total = int(ref["count"].sum())
     assert total > 50
-    e, p, st = _run(api, api.QED_F64, f, pos, 500.0, 10.0, 1.0, 5, 1, total + 100)
+    prec = api.QED_F64 if prec_name == "f64" else api.QED_F32
+    e, p, st = _run(api, prec, f, pos, 500.0, 10.0, 1.0, 5, 1, total + 100)
     assert st["schwinger_pairs"] == total
     assert np.array_equal(np.sort(e["id"]), np.sort(ref["e_id"]))
