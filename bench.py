@@ -345,6 +345,16 @@ def e2e_leg(api, t, bufs, fire, steps, ws, pinned):
     bo = sum(v.numel() * v.element_size() for d in out.values() for v in d.values()) + counts_h.numel() * 8
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_step = counts(bufs)
+    # warm-up, untimed: one pass of every copy in both directions through both
+    # buffer sets (the first transfers from newly pinned pages run at a third of
+    # the link's rate)
+    for b, _ in sets:
+        for k in host:
+            n = host[k]["px"].numel()
+            for c in names_in:
+                b[k].arrays[c][:n].copy_(host[k][c], non_blocking=True)
+            for c in names_out:
+                out[k][c].copy_(b[k].arrays[c][:n], non_blocking=True)
     barrier(ws)
     torch.cuda.synchronize()
     t0.record(s_in)
