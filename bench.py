@@ -395,6 +395,77 @@ def e2e_leg(api, t, bufs, fire, steps, ws, pinned):
     return ms, n_step, bi, bo
 
 
+def batched_leg(api, tabs, ws, steps=10, warmup=3):
+    """The batched substep (qed_substep_batched) on the many-patch workload:
+    64 patches of round(10^(3+4U)) particles (seed 7; sum ~7e7), half
+    electrons, half photons, the §4 distribution with its stored fields; CUDA
+    events around each step and around its evolution launch."""
+    import torch
+
+    from paper_2110_00256_gb300 import workloads
+    sizes = workloads.patch_counts(64, 7)
+    patches, off = [], 0
+    for i, c in enumerate(sizes):
+        c = int(c)
+        p = {}
+        for k, m, s in (("electrons", c // 2, 1), ("photons", c - c // 2, 2)):
+            b = api.SpeciesBuffers(m + max(256, m // 20), api.QED_F32)
+            d = workloads.paper_benchmark_torch(m, SEED + 100 * i + s, off, dtype=torch.float32)
+            for col, v in d.items():
+                b.arrays[col][:m].copy_(v)
+            del d
+            b.count.fill_(m)
+            off += m
+            p[k] = b
+        p["positrons"] = api.SpeciesBuffers(max(256, c // 20), api.QED_F32)
+        p["fire"] = [api.FireBuffers(p[k].capacity) for k in ("electrons", "positrons", "photons")]
+        patches.append(p)
+    b = api.Batch(patches, api.QED_F32)
+    stats = api.Stats()
+    opts = api.make_opts(stats=stats)
+    for s in range(warmup):
+        api.qed_substep_batched(tabs, b, DT, SEED, s, opts)
+    torch.cuda.synchronize()
+    live = sum(int(p[k].count.item()) for p in patches for k in ("electrons", "positrons", "photons"))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    st = torch.cuda.current_stream()
+    for a, e in evs:
+        a.record(st), e.record(st)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0 = stats.as_dict()["evolved"]
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for s in range(steps):
+        opts.evolve_begin, opts.evolve_end = evs[s][0].cuda_event, evs[s][1].cuda_event
+        api.qed_substep_batched(tabs, b, DT, SEED, warmup + s, opts)
+    t1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ws, t0.elapsed_time(t1))
+    evolved = stats.as_dict()["evolved"] - ev0
+    ev_ms = sum(a.elapsed_time(e) for a, e in evs) / steps
+    gbs = BYTES_F32 * (evolved / steps) / (ev_ms * 1e-3) / 1e9
+    hbm, which = peaks()
+    # the same steps with the direct-load kernel (16-byte loads into registers), for comparison
+    od = api.make_opts(stats=stats, evolve_pipeline=api.QED_EVOLVE_DIRECT)
+    dms, evd0 = [], stats.as_dict()["evolved"]
+    for s in range(steps):
+        od.evolve_begin, od.evolve_end = evs[s][0].cuda_event, evs[s][1].cuda_event
+        api.qed_substep_batched(tabs, b, DT, SEED, warmup + steps + s, od)
+        torch.cuda.synchronize()
+        dms.append(evs[s][0].elapsed_time(evs[s][1]))
+    out = {"value": sum_over_ranks(ws, evolved) / (ms * 1e-3), "unit": UNIT, "patches": len(patches),
+           "particles": live, "ms_per_step": ms / steps, "launches_per_step": 4, "evolve_ms": round(ev_ms, 4),
+           "evolve_hbm_gbs": round(gbs, 1), "evolve_frac": round(gbs / hbm, 4), "peak_kind": which,
+           "direct_loads_evolve_hbm_gbs": round(BYTES_F32 * ((stats.as_dict()["evolved"] - evd0) / steps) /
+                                                (sum(dms) / steps * 1e-3) / 1e9, 1),
+           "workload": "64 patches, counts round(10^(3+4U)) (seed 7), half e-, half photons, paper §4 distribution, "
+                       "FP32, stored fields"}
+    del patches, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def schwinger_leg(api, ws):
     """Schwinger pairs per cell (qed_schwinger_pairs) on 1e8 FP32 cells: fields
     of PIC strength (components N(0, 1e-3) E_s: the rate underflows, the FP32
@@ -597,6 +668,9 @@ def gpu_main(args):
                              "workload": "64 patches, counts round(10^(3+4U)) x %g (seed 7), e- beam gamma 2000 +-5%% "
                                          "vs a0=100 linear plane wave (0.8 um), dt = T_L/200, photons < 2 m_e c^2 "
                                          "discarded" % args.cascade_scale}
+
+    if not args.no_cascade:
+        result["batched"] = batched_leg(api, tabs, ws)
 
     if not args.no_schwinger:
         result.setdefault("paths", {})["schwinger"] = schwinger_leg(api, ws)

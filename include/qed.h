@@ -340,10 +340,13 @@ qed_status qed_substep_batched(const qed_tables *t, const qed_batch *b, double d
                                int64_t step, const qed_substep_opts *opts, void *stream);
 
 /* Launch-shape tuner: times the evolution kernel of `b` (dry runs that read
- * everything and store nothing, so the particles are untouched) for 128, 256
- * and 512 threads per CTA and every CTA count per SM the registers allow, and
- * keeps the fastest in `b` (used by qed_substep_batched unless opts override
- * it).  Outputs may be NULL.  Synchronises `stream`. */
+ * everything and store nothing, so the particles are untouched): for an FP32
+ * batch with 16-byte-aligned arrays the default bulk-copy kernel (a producer
+ * warp streams tiles into shared memory), then direct loads with 128, 256 and
+ * 512 threads per CTA and every CTA count per SM the registers allow; keeps the
+ * fastest in `b` (used by qed_substep_batched unless opts override it).
+ * *threads_out = *ctas_per_sm_out = 0 when the default was the fastest.
+ * Outputs may be NULL.  Synchronises `stream`. */
 qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t *threads_out,
                            int32_t *ctas_per_sm_out, float *ms_out, void *stream);
 

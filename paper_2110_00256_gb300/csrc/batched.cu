@@ -13,7 +13,8 @@
 #include <vector>
 
 #include "events.cuh"
-#include "evolve.cuh"
+#include "evolve_core.cuh"
+#include "pipeline.cuh"
 #include "pusher.cuh"
 
 namespace qed {
@@ -191,6 +192,187 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4)
     flush_counts(cb.stats, kb, false);
 }
 
+// ---------------------------------------------------------------------------
+// The evolution over device-resident segments, FP32 with 16-byte-aligned
+// arrays: the bulk-copy form of the single-call default.  The last warp of the
+// CTA copies whole tiles (TP = CW x 32 x 4 particles of one segment) of the
+// eleven streamed arrays into S shared-memory stages with cp.async.bulk; the CW
+// consumer warps take four particles each, release the stage and evaluate them
+// (the ragged last tile of a segment is read from global memory).  Tiles map
+// to segments through the block-wide prefix of their tile counts.  Every wait
+// is bounded (QED_STAT_WAIT_TIMEOUT counts a CTA that gave up).
+// ---------------------------------------------------------------------------
+constexpr int kSegArrays = 11;
+
+__device__ __forceinline__ const float *seg_stream(const EvolveSeg<float> &g, int k)
+{
+    switch (k) {
+    case 0: return g.px;
+    case 1: return g.py;
+    case 2: return g.pz;
+    case 3: return g.ex;
+    case 4: return g.ey;
+    case 5: return g.ez;
+    case 6: return g.bx;
+    case 7: return g.by;
+    case 8: return g.bz;
+    case 9: return g.tau;
+    default: return g.tau_c;
+    }
+}
+
+__device__ __forceinline__ bool seg_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort || clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void seg_give_up(int *abort, long long *stats)
+{
+    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+}
+
+template <int CW, int S>
+__global__ void __launch_bounds__((CW + 1) * 32, 1)
+    evolve_seg_bulk_kernel(const EvolveSeg<float> *__restrict__ segs, int n_seg, TablesView<float> tab, float dt,
+                           float cut_qs, float cut_bw, long long *stats, int dry)
+{
+    constexpr int THREADS = (CW + 1) * 32;
+    constexpr int TP = CW * 32 * 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *s_stage = reinterpret_cast<float *>(smem_raw);  // [S][kSegArrays][TP]
+    long long *s_end = reinterpret_cast<long long *>(smem_raw + (size_t)S * kSegArrays * TP * sizeof(float));
+    long long *s_n = s_end + n_seg;
+    __shared__ __align__(8) uint64_t s_full[S];
+    __shared__ __align__(8) uint64_t s_empty[S];
+    __shared__ float s_qs[QED_MAX_TABLE_N];
+    __shared__ float s_bw[QED_MAX_TABLE_N];
+    __shared__ long long s_warp[THREADS / 32];
+    __shared__ int s_abort;
+
+    for (int i = threadIdx.x; i < tab.qs_G.n; i += THREADS) s_qs[i] = tab.qs_G.ln_f[i];
+    for (int i = threadIdx.x; i < tab.bw_T.n; i += THREADS) s_bw[i] = tab.bw_T.ln_f[i];
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&s_full[k], 1);
+            mbar_init(&s_empty[k], CW);
+        }
+        mbar_fence_init();
+    }
+    const long long total = tile_prefix<float, THREADS>(segs, n_seg, TP, s_end, s_n, s_warp);  // ends with a barrier
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = &s_abort;
+
+    if (warp == CW) {  // producer
+        const uint64_t pol = l2_evict_first();
+        int k = 0, s = 0;
+        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+            const int st = k % S;
+            const uint32_t ph = (uint32_t)(k / S) & 1u;
+            while (s_end[s] <= t) ++s;  // tiles ascend: the segment only moves forward
+            const int64_t i0 = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
+            if (!__all_sync(0xffffffffu, seg_wait(&s_empty[st], ph ^ 1u, abort))) {
+                if (lane == 0) seg_give_up(&s_abort, stats);
+                break;
+            }
+            if (i0 + TP <= s_n[s]) {
+                if (lane == 0) mbar_arrive_expect_tx(&s_full[st], kSegArrays * TP * (uint32_t)sizeof(float));
+                __syncwarp();
+                if (lane < kSegArrays)
+                    bulk_g2s(s_stage + ((size_t)st * kSegArrays + lane) * TP, seg_stream(segs[s], lane) + i0,
+                             TP * (uint32_t)sizeof(float), &s_full[st], pol);
+            } else if (lane == 0) {
+                mbar_arrive(&s_full[st]);
+            }
+        }
+        for (int j = 1; j <= S && j <= k; ++j) {
+            const int kk = k - j;
+            if (!mbar_wait(&s_full[kk % S], (uint32_t)(kk / S) & 1u) && lane == 0) seg_give_up(&s_abort, stats);
+        }
+        return;
+    }
+
+    int bad = 0;
+    int k = 0, s = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int st = k % S;
+        const uint32_t ph = (uint32_t)(k / S) & 1u;
+        while (s_end[s] <= t) ++s;
+        const EvolveSeg<float> &sg = segs[s];
+        const int64_t n = s_n[s];
+        const int64_t base = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
+        const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+        if (!__all_sync(0xffffffffu, seg_wait(&s_full[st], ph, abort))) {
+            if (lane == 0) seg_give_up(&s_abort, stats);
+            break;
+        }
+        float px[4], py[4], pz[4], ex[4], ey[4], ez[4], bx[4], by[4], bz[4], tau[4], tc[4];
+        bool full4;
+        if (base + TP <= n) {
+            const float4 *v = reinterpret_cast<const float4 *>(s_stage + (size_t)st * kSegArrays * TP) + threadIdx.x;
+            constexpr int q = TP / 4;
+            float4 w;
+#define QED_UNPACK(arr, kk)                                \
+    w = v[(kk) * q];                                       \
+    arr[0] = w.x, arr[1] = w.y, arr[2] = w.z, arr[3] = w.w;
+            QED_UNPACK(px, 0) QED_UNPACK(py, 1) QED_UNPACK(pz, 2);
+            QED_UNPACK(ex, 3) QED_UNPACK(ey, 4) QED_UNPACK(ez, 5);
+            QED_UNPACK(bx, 6) QED_UNPACK(by, 7) QED_UNPACK(bz, 8);
+            QED_UNPACK(tau, 9) QED_UNPACK(tc, 10);
+#undef QED_UNPACK
+            full4 = true;
+        } else {
+            full4 = i0 + 4 <= n;
+            if (full4) {
+                load_vec<float, 4>(sg.px, i0, px);
+                load_vec<float, 4>(sg.py, i0, py);
+                load_vec<float, 4>(sg.pz, i0, pz);
+                load_vec<float, 4>(sg.ex, i0, ex);
+                load_vec<float, 4>(sg.ey, i0, ey);
+                load_vec<float, 4>(sg.ez, i0, ez);
+                load_vec<float, 4>(sg.bx, i0, bx);
+                load_vec<float, 4>(sg.by, i0, by);
+                load_vec<float, 4>(sg.bz, i0, bz);
+                load_vec<float, 4>(sg.tau, i0, tau);
+                load_vec<float, 4>(sg.tau_c, i0, tc);
+            } else {
+                load_scalar<float, 4>(sg, n, i0, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[st]);
+        evolve_regs<float, 4>(sg, n, i0, full4, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt,
+                              sg.proc == QED_PROC_QS ? cut_qs : cut_bw, stats, dry, bad);
+    }
+    if (stats && !dry) warp_count(stats + QED_STAT_NONFINITE, bad);
+}
+
+// 15 consumer warps + the producer (16 warps, one CTA per SM), 2 stages, as the single-call default
+constexpr int kSegBulkCW = 15, kSegBulkS = 2;
+
+static qed_status launch_evolve_seg_bulk(const EvolveSeg<float> *segs, int n_seg, const TablesView<float> &tab,
+                                         float dt, float cut_qs, float cut_bw, long long *stats, int dry,
+                                         cudaStream_t st)
+{
+    constexpr size_t stage = (size_t)kSegBulkS * kSegArrays * kSegBulkCW * 32 * 4 * sizeof(float);
+    const size_t dyn = stage + (size_t)n_seg * 2 * sizeof(long long);
+    auto k = evolve_seg_bulk_kernel<kSegBulkCW, kSegBulkS>;
+    static bool attr = false;
+    if (!attr) {
+        QED_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(stage + 3 * QED_MAX_PATCHES * 2 * sizeof(long long))));
+        attr = true;
+    }
+    k<<<sm_count(), (kSegBulkCW + 1) * 32, dyn, st>>>(segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
+
 // CTAs of 256 threads for `warps` warp chunks of work, at most the resident count
 static int resident_grid(int64_t warps, int per_sm)
 {
@@ -345,13 +527,26 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
     QED_LAUNCH_CHECK();
     const int threads = (o && o->evolve_threads) ? o->evolve_threads : (b->threads ? b->threads : 256);
     const int ctas = (o && o->evolve_ctas_per_sm) ? o->evolve_ctas_per_sm : b->ctas_per_sm;
+    // the default shape (nothing asked for, nothing tuned) of an FP32 batch with
+    // aligned arrays: the bulk-copy kernel
+    const bool bulk = sizeof(T) == 4 && b->vec && !(o && (o->evolve_threads || o->evolve_ctas_per_sm)) &&
+                      !(o && o->evolve_pipeline == QED_EVOLVE_DIRECT) && b->threads == 0 && b->ctas_per_sm == 0;
     if (o && o->evolve_begin) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_begin, st));
     const T cut_qs = o ? (T)o->qs_chi_cut : T(0), cut_bw = o ? (T)o->bw_chi_cut : T(0);
-    qed_status s = wave ? launch_push_evolve<T>((const EvolveSeg<T> *)b->d_evolve, b->d_push, 3 * n, make_view<T>(t),
-                                                wave_params(wave), t0, dt, o ? o->d_step : nullptr, step, cut_qs,
-                                                cut_bw, stats, store_fields, b->push_vec, st)
-                        : launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
-                                                    cut_qs, cut_bw, stats, 0, b->vec, threads, ctas, st);
+    qed_status s;
+    if (wave) {
+        s = launch_push_evolve<T>((const EvolveSeg<T> *)b->d_evolve, b->d_push, 3 * n, make_view<T>(t),
+                                  wave_params(wave), t0, dt, o ? o->d_step : nullptr, step, cut_qs, cut_bw, stats,
+                                  store_fields, b->push_vec, st);
+    } else if constexpr (sizeof(T) == 4) {
+        s = bulk ? launch_evolve_seg_bulk((const EvolveSeg<float> *)b->d_evolve, 3 * n, make_view<float>(t),
+                                          (float)dt, cut_qs, cut_bw, stats, 0, st)
+                 : launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
+                                             cut_qs, cut_bw, stats, 0, b->vec, threads, ctas, st);
+    } else {
+        s = launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt, cut_qs,
+                                      cut_bw, stats, 0, b->vec, threads, ctas, st);
+    }
     if (s) return s;
     if (o && o->evolve_end) QED_CUDA_TRY(cudaEventRecord((cudaEvent_t)o->evolve_end, st));
     const bool mlp = o && o->sampler == 1;
@@ -473,6 +668,20 @@ extern "C" qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t
     const int cand_threads[3] = {128, 256, 512};
     float best = 1e30f;
     int bt = 256, bc = 0;
+    if (b->prec == QED_F32 && b->vec) {  // the default: the bulk-copy kernel (reported as 0, 0)
+        float tot = 0.f;
+        for (int rep = 0; rep < 4 && s == QED_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            s = launch_evolve_seg_bulk((const EvolveSeg<float> *)b->d_evolve, 3 * b->n_patches, make_view<float>(t),
+                                       0.f, 0.f, 0.f, nullptr, 1, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (s == QED_OK) best = tot / 3, bt = 0, bc = 0;
+    }
     for (int th : cand_threads) {
         const int max_ctas = 768 / th;  // the register budget of the kernel's launch bounds
         for (int c = 1; c <= max_ctas && s == QED_OK; ++c) {

@@ -95,7 +95,10 @@ def test_tuner_leaves_particles_untouched(api, tables):
     b = api.Batch(bat, api.QED_F32)
     res = api.qed_tune_evolve(tables, b)
     torch.cuda.synchronize()
-    assert res["threads"] in (128, 256, 512) and 1 <= res["ctas_per_sm"] <= 6 and res["ms"] > 0
+    # the default bulk-copy kernel (0, 0) or a direct-load shape
+    assert (res["threads"], res["ctas_per_sm"]) == (0, 0) or \
+        (res["threads"] in (128, 256, 512) and 1 <= res["ctas_per_sm"] <= 6)
+    assert res["ms"] > 0
     for p, bf in zip(bat, before):
         for k in SPECIES:
             a = _sorted(p[k])
