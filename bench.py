@@ -171,24 +171,27 @@ def barrier(ws):
         dist.barrier()
 
 
+def _reduce(x: float, op) -> float:
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"  # (gloo: the host-side tests)
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def max_over_ranks(ws, x: float) -> float:
     if ws == 1:
         return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(x, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(ws, x: float) -> float:
     if ws == 1:
         return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, dist.ReduceOp.SUM)
 
 
 # ----------------------------------------------------------------------------------------

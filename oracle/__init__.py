@@ -12,6 +12,7 @@ The numerics live in plain C (``oracle/*.c``), compiled with gcc into
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
 import os
 import subprocess
 import threading
@@ -358,7 +359,8 @@ def tables(qs_chi_min=1e-3, qs_chi_max=1e3, qs_n_chi=256, qs_n_xi=256, qs_xi_min
     t = OracleTables(qs_chi_min, qs_chi_max, qs_n_chi, qs_n_xi, qs_xi_min,
                      bw_chi_min, bw_chi_max, bw_n_chi, bw_n_xi)
     key = "_".join(f"{t.params[k]!r}" for k in sorted(t.params))
-    path = os.path.join(_CACHE_DIR, f"t_{abs(hash(key)) % (1 << 40):x}_{qs_n_chi}x{qs_n_xi}.npz")
+    # (a digest of the parameters: Python's hash() of a string differs from process to process)
+    path = os.path.join(_CACHE_DIR, f"t_{hashlib.sha1(key.encode()).hexdigest()[:16]}_{qs_n_chi}x{qs_n_xi}.npz")
     if cache and os.path.exists(path):
         loaded = OracleTables.load(path)
         if loaded.params == t.params:
