@@ -197,7 +197,7 @@ double oracle_bw_upper_half(double chig)
     return s;
 }
 
-/* exact cumulative distributions by direct quadrature, used to judge sampling:
+/* exact cumulative distributions by direct quadrature, used to test sampling:
  * QS P(chi, xi), xi in (0, 1]; BW P(chi_g, xi), xi in [0, 1] */
 double oracle_qs_cdf(double chi, double xi)
 {

@@ -10,7 +10,7 @@ relative to the scale of the terms that form them:
     uncertainty produces through the oracle's table lookup, plus tol * rate);
   - a firing decision may differ only where the oracle's new optical depth lies
     within that bound of zero (and, in FP64, within the stated 1e-6 margin);
-  - an FP32 inverse-CDF sample is judged by its backward error: the r that the
+  - an FP32 inverse-CDF sample is assessed by its backward error: the r that the
     oracle's FP64 table maps to the sampled xi must lie within 1e-5 (relative)
     of the drawn uniform.
 """
@@ -116,7 +116,7 @@ def check_substep_fp32(ot, host, got, fire_lists, dt, seed, step, rtol_r=1e-5):
     """Element-wise check of one FP32 substep (see module docstring).
     host: pre-step state as FP64 (from the FP32 inputs); got: GPU state after;
     fire_lists: species -> (indices, chi) of the GPU firing lists.  The sample
-    of a firing particle is judged at the chi the GPU evaluated (its own error
+    of a firing particle is assessed at the chi the GPU evaluated (its own error
     is bounded separately, against the oracle's chi)."""
     procs = {"electrons": 0, "positrons": 0, "photons": 1}
     gpu = {k: {kk: v for kk, v in got[k].items()} for k in got}
