@@ -269,11 +269,14 @@ qed_status qed_generate_pairs(const qed_tables *t, const qed_species *photons,
                               const qed_fire_list *fire, uint64_t seed, int64_t step,
                               const qed_substep_opts *opts, qed_precision prec, void *stream);
 
-/* The whole substep on three species: one batched evolution launch over
- * electrons (QS), positrons (QS) and photons (BW), then pair production, then
- * photon emission.  fire[0..2] are the firing lists of the three species in
- * that order.  Products are appended after the live particles and are first
- * evolved in the next call.  Graph-capturable. */
+/* The whole substep on three species in four launches: zero the firing
+ * counts; one evolution launch over electrons (QS), positrons (QS) and photons
+ * (BW); one event launch for the three firing lists (photon emission of both
+ * leptons and pair production side by side: they touch disjoint particles;
+ * with the learned sampler, one launch per list); clamp the counts.  fire[0..2]
+ * are the firing lists of the three species in that order.  Products are
+ * appended after the live particles and are first evolved in the next call.
+ * Graph-capturable. */
 qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        const qed_species *positrons, const qed_species *photons, double dt,
                        uint64_t seed, int64_t step, const qed_substep_opts *opts,
@@ -328,14 +331,16 @@ qed_status qed_batch_create(const qed_patch *patches, int32_t n_patches, qed_pre
                             qed_batch **out, void *stream);
 qed_status qed_batch_destroy(qed_batch *b);
 
-/* qed_substep for every patch of `b` (§3, §5), in five launches whatever the
- * number of patches: zero the firing counts; one persistent evolution launch
- * over all 3 x n species segments (tiles of every segment form one index
- * space, so uneven patches share the grid); one pair-production launch over
- * all photon firing lists; one photon-emission launch over all lepton firing
- * lists; one launch clamping the counts (and advancing opts->d_step).  Stream-
- * ordered, allocates nothing, graph-capturable.  Results per patch are those
- * of qed_substep on that patch. */
+/* qed_substep for every patch of `b` (§3, §5), in four launches whatever the
+ * number of patches: zero the firing counts (and add the live counts to
+ * QED_STAT_EVOLVED); one persistent evolution launch over all 3 x n species
+ * segments (tiles of every segment form one index space, so uneven patches
+ * share the grid; FP32 with aligned arrays streams them through shared memory
+ * by default); one event launch over all firing lists (photon emission of the
+ * leptons and pair production of the photons side by side; with the learned
+ * sampler, one launch per process); one launch clamping the counts (and
+ * advancing opts->d_step).  Stream-ordered, allocates nothing,
+ * graph-capturable.  Results per patch are those of qed_substep on that patch. */
 qed_status qed_substep_batched(const qed_tables *t, const qed_batch *b, double dt, uint64_t seed,
                                int64_t step, const qed_substep_opts *opts, void *stream);
 
