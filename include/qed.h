@@ -388,8 +388,9 @@ qed_status qed_push_batched(const qed_batch *b, const qed_plane_wave *wave, doub
  * evolves the optical depth on the same registers, so that positions, momenta
  * and optical depths cross HBM once per step.  The particles end bit for bit as
  * with the two separate calls; the species' E and B arrays are written only if
- * store_fields != 0 (products then inherit stale fields, which the next step's
- * push replaces before any use).  Graph-capturable. */
+ * store_fields != 0 (otherwise they are left alone, and the photons emitted
+ * get no field values: the next step computes every particle's fields before
+ * any use).  Graph-capturable. */
 qed_status qed_push_substep_batched(const qed_tables *t, const qed_batch *b, const qed_plane_wave *wave,
                                     double t0, double dt, uint64_t seed, int64_t step,
                                     const qed_substep_opts *opts, int32_t store_fields, void *stream);

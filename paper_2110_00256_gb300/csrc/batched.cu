@@ -555,9 +555,12 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
             return s;
         if ((s = launch_events_batched<T, true>(b, event_common<T>(t, QED_PROC_QS, seed, step, o), true, st)))
             return s;
-    } else if ((s = launch_events_batched_all<T>(b, event_common<T>(t, QED_PROC_QS, seed, step, o),
-                                                   event_common<T>(t, QED_PROC_BW, seed, step, o), st))) {
-        return s;
+    } else {
+        // the push fused into the evolution without stored fields computes every
+        // particle's fields itself: the photons emitted get none
+        EventCommon<T> cq = event_common<T>(t, QED_PROC_QS, seed, step, o);
+        cq.copy_fields = (wave && !store_fields) ? 0 : 1;
+        if ((s = launch_events_batched_all<T>(b, cq, event_common<T>(t, QED_PROC_BW, seed, step, o), st))) return s;
     }
     clamp_batch_kernel<<<(6 * n + 255) / 256, 256, 0, st>>>(b->d_clamp, 6 * n, o ? o->d_step : nullptr);
     QED_LAUNCH_CHECK();

@@ -143,6 +143,7 @@ EventCommon<T> event_common(const qed_tables *t, int proc, uint64_t seed, int64_
     c.d_step = o ? o->d_step : nullptr;
     c.threshold = o ? o->photon_threshold : 0.0;
     c.stats = o ? (long long *)o->d_stats : nullptr;
+    c.copy_fields = 1;
     if (o && o->sampler == 1) c.mlpv = mlp_view((const qed_mlp *)o->mlp, proc);
     return c;
 }

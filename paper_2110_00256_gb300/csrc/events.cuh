@@ -57,6 +57,7 @@ struct EventCommon {
     const int64_t *d_step;    // if set, the step is read from here
     double threshold;
     long long *stats;
+    int copy_fields;          // 0: products get no field values (the caller computes them, see qed_push_substep_batched)
 };
 
 struct EventCounts {
@@ -65,11 +66,14 @@ struct EventCounts {
 
 template <typename T>
 __device__ __forceinline__ void write_particle(const SpeciesPtrs<T> &d, int64_t k, T px, T py, T pz, T ex, T ey,
-                                               T ez, T bx, T by, T bz, T w, uint64_t id, double tau)
+                                               T ez, T bx, T by, T bz, T w, uint64_t id, double tau,
+                                               bool fields = true)
 {
     d.px[k] = px, d.py[k] = py, d.pz[k] = pz;
-    d.ex[k] = ex, d.ey[k] = ey, d.ez[k] = ez;
-    d.bx[k] = bx, d.by[k] = by, d.bz[k] = bz;
+    if (fields) {
+        d.ex[k] = ex, d.ey[k] = ey, d.ez[k] = ez;
+        d.bx[k] = bx, d.by[k] = by, d.bz[k] = bz;
+    }
     d.w[k] = w;
     d.id[k] = id;
     store_tau<T>(d.tau, d.tau_c, k, tau);
@@ -145,8 +149,10 @@ __device__ __forceinline__ void qs_event_chunk(const EventSeg<T> &g, const Event
     if (keep && room) {
         const U4 cid = draw(c.seed, pid, step, kChildId);
         const uint64_t child = ((uint64_t)cid.y << 32) | cid.x;
-        write_particle<T>(G, slot, gg * nx, gg * ny, gg * nz, P.ex[i], P.ey[i], P.ez[i], P.bx[i], P.by[i], P.bz[i],
-                          P.w[i], child, tau_draw(c.seed, child, step, kTauInit));
+        const bool f = c.copy_fields != 0;
+        write_particle<T>(G, slot, gg * nx, gg * ny, gg * nz, f ? P.ex[i] : T(0), f ? P.ey[i] : T(0),
+                          f ? P.ez[i] : T(0), f ? P.bx[i] : T(0), f ? P.by[i] : T(0), f ? P.bz[i] : T(0), P.w[i],
+                          child, tau_draw(c.seed, child, step, kTauInit), f);
         copy_position<T>(G, slot, P, i);
     }
     if (exec) {
