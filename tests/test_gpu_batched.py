@@ -182,3 +182,28 @@ def test_batched_bulk_equals_direct_loads(api, tables):
     assert sa.as_dict()["dropped_capacity"] == 0
     for pa, pb in zip(a, b):
         _assert_same(pa, pb)
+
+
+def test_maximum_patch_count(api, tables):
+    """QED_MAX_PATCHES patches (3072 segments: the largest shared-memory prefix
+    of the batched kernels) of a few particles each: the bulk-copy evolution
+    equals the direct-load one, every particle is counted once, and a second
+    batch of the same patches one over the maximum is refused."""
+    from paper_2110_00256_gb300 import _lib
+    n_max = _lib.QED_MAX_PATCHES
+    rng = np.random.default_rng(5)
+    sizes = list(rng.integers(0, 9, n_max))
+    host = _host_patches(sizes, 41, tau_scale=0.05)
+    a = _device_patches(api, host, api.QED_F32)
+    b = _device_patches(api, host, api.QED_F32)
+    ba, bb = api.Batch(a, api.QED_F32), api.Batch(b, api.QED_F32)
+    sa, sb = api.Stats(), api.Stats()
+    api.qed_substep_batched(tables, ba, 10.0, 6, 0, api.make_opts(stats=sa))
+    api.qed_substep_batched(tables, bb, 10.0, 6, 0, api.make_opts(stats=sb, evolve_pipeline=api.QED_EVOLVE_DIRECT))
+    torch.cuda.synchronize()
+    live = sum(len(h[k]["px"]) for h in host for k in SPECIES)
+    assert sa.as_dict() == sb.as_dict() and sa.as_dict()["evolved"] == live
+    for pa, pb in zip(a, b):
+        _assert_same(pa, pb)
+    with pytest.raises(api.QedError):
+        api.Batch(a + a[:1], api.QED_F32)
