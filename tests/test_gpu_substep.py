@@ -298,3 +298,60 @@ def test_evolution_variants_equal_direct_loads(api, tabs, variant):
     for k in SPECIES:
         for c in da[k]:
             assert np.array_equal(da[k][c], db[k][c]), (k, c)
+
+
+def test_full_size_batched_workload_sampled(api, tabs):
+    """The many-patch workload at full size (64 patches of round(10^(3+4U))
+    particles, seed 7: 6.4e7 in all, half electrons, half photons), one FP32
+    batched substep in the benchmark's configuration (the bulk-copy evolution
+    over device-resident segments); 2000 sampled particles of each of 8 patches
+    are recomputed by the oracle from their pre-step state."""
+    from paper_2110_00256_gb300 import workloads
+    ot, t = tabs
+    sizes = workloads.patch_counts(64, 7)
+    patches, picks, off = [], [], 0
+    order = np.argsort(sizes)[::-1]
+    sampled = set(order[:4].tolist()) | set(order[30:34].tolist())  # the largest and some mid-sized
+    for i, c in enumerate(sizes):
+        c = int(c)
+        p = {}
+        for k, m, s in (("electrons", c // 2, 1), ("photons", c - c // 2, 2)):
+            b = api.SpeciesBuffers(m + max(256, m // 20), api.QED_F32)
+            d = workloads.paper_benchmark_torch(m, 100 * i + s, off, dtype=torch.float32)
+            for col, v in d.items():
+                b.arrays[col][:m].copy_(v)
+            del d
+            b.count.fill_(m)
+            off += m
+            p[k] = b
+        p["positrons"] = api.SpeciesBuffers(max(256, c // 20), api.QED_F32)
+        p["fire"] = [api.FireBuffers(p[k].capacity) for k in SPECIES]
+        patches.append(p)
+        if i in sampled:
+            for k, proc in (("electrons", 0), ("photons", 1)):
+                n = int(p[k].count.item())
+                idx = workloads.subsample_ids(n, min(n, 2000), 11 + i)
+                ti = torch.as_tensor(idx, device="cuda")
+                pre = {col: p[k].arrays[col][ti].cpu().numpy() for col in FIELDS + ("tau", "tau_c", "weight", "id")}
+                picks.append((i, k, proc, idx, ti, pre))
+    b = api.Batch(patches, api.QED_F32)
+    stats = api.Stats()
+    api.qed_substep_batched(t, b, 10.0, 77, 0, api.make_opts(stats=stats))
+    torch.cuda.synchronize()
+    st = stats.as_dict()
+    assert st["nonfinite"] == 0 and st["dropped_capacity"] == 0 and st["fire_overflow"] == 0
+    assert st["evolved"] == int(sizes.sum()) and st["qs_events"] > 0
+    fired_total = 0
+    for i, k, proc, idx, ti, pre in picks:
+        p = {c: v.astype(np.float64) if c != "id" else v.view(np.uint64) for c, v in pre.items()}
+        tau_new, chi, rate, f = oracle.evolve(proc, ot, p, 10.0)
+        bound = tau_bound(ot, proc, p, chi, rate, 10.0, 1e-5)
+        arr = patches[i][k].arrays
+        post_tau = arr["tau"][ti].cpu().double().numpy() - arr["tau_c"][ti].cpu().double().numpy()
+        fl = patches[i]["fire"][0 if k == "electrons" else 2]
+        gpu_fired = np.isin(idx, fl.idx[:fl.n()].cpu().numpy())
+        assert np.all(np.abs(tau_new[gpu_fired != f]) <= bound[gpu_fired != f]), (i, k)
+        quiet = ~f & ~gpu_fired
+        assert np.all(np.abs(post_tau[quiet] - tau_new[quiet]) <= bound[quiet]), (i, k)
+        fired_total += int(f.sum())
+    assert fired_total > 0
