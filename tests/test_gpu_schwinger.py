@@ -100,3 +100,46 @@ def test_schwinger_weak_and_strong_field_mix(api, prec_name):
     e, p, st = _run(api, prec, f, pos, 500.0, 10.0, 1.0, 5, 1, total + 100)
     assert st["schwinger_pairs"] == total
     assert np.array_equal(np.sort(e["id"]), np.sort(ref["e_id"]))
+
+
+def test_full_size_schwinger_sampled(api):
+    """1e8 FP32 cells (the benchmark's size; fields N(0, 0.12) E_s, so that a
+    few percent of the cells make pairs) through the streamed kernel; for 3000
+    sampled cells the oracle's count and pair ids from the cell's own fields
+    and index.  Cells carry their index in (x, y), which the pairs inherit."""
+    from paper_2110_00256_gb300 import workloads
+    n = 100_000_000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(23)
+    f = {k: torch.randn(n, generator=g, device="cuda", dtype=torch.float32) * 0.12
+         for k in ("ex", "ey", "ez", "bx", "by", "bz")}
+    cell = torch.arange(n, device="cuda")
+    pos = {"x": torch.div(cell, 16384, rounding_mode="floor").float(), "y": (cell % 16384).float(),
+           "z": torch.zeros(n, device="cuda")}
+    del cell
+    e = api.SpeciesBuffers(3_000_000, api.QED_F32, positions=True)
+    p = api.SpeciesBuffers(3_000_000, api.QED_F32, positions=True)
+    stats = api.Stats()
+    dv, dt, w, seed, step = 5e4, 10.0, 1.0, 21, 5  # ~1e6 pairs in all
+    api.qed_schwinger_pairs(f, dv, dt, w, seed, step, e, p, stats=stats, positions=pos)
+    torch.cuda.synchronize()
+    st = stats.as_dict()
+    assert st["dropped_capacity"] == 0 and st["schwinger_pairs"] > 100_000
+    idx = workloads.subsample_ids(n, 3000, 9)
+    ti = torch.as_tensor(idx, device="cuda")
+    fh = {k: v[ti].cpu().numpy().astype(np.float64) for k, v in f.items()}
+    del f, pos
+    eh = e.to_host()
+    gpu_cell = eh["x"].astype(np.int64) * 16384 + eh["y"].astype(np.int64)
+    sel = np.isin(gpu_cell, idx)
+    got = dict(zip(*np.unique(gpu_cell[sel], return_counts=True)))
+    want_ids, made = set(), 0
+    for j, c in enumerate(idx.tolist()):
+        lam = oracle.schwinger_rate([fh[k][j] for k in ("ex", "ey", "ez")], [fh[k][j] for k in ("bx", "by", "bz")]) \
+            * dv * dt / w
+        k = oracle.poisson(lam, seed, c, step)
+        assert got.get(c, 0) == k, (c, lam, k, got.get(c, 0))
+        made += k
+        want_ids.update(oracle.schwinger_pair_ids(seed, c, step, i)[0] for i in range(k))
+    assert made > 10
+    assert set(eh["id"][sel].tolist()) == want_ids
