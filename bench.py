@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
     ap.add_argument("--no-schwinger", action="store_true")
+    ap.add_argument("--no-longrun", action="store_true")
     ap.add_argument("--cascade-scale", type=float, default=0.1,
                     help="fraction of the 64 patch counts round(10^(3+4U)) to run in the cascade leg")
     ap.add_argument("--cascade-steps", type=int, default=2000)
@@ -476,6 +477,81 @@ def batched_leg(api, tabs, ws, steps=10, warmup=3):
     return out
 
 
+def chi_for_inputs(d, photon):
+    """chi of the unscaled synthetic particles (§2 definition, FP64 numpy), only
+    to rescale their fields so that chi follows the workload's distribution."""
+    import numpy as np
+    p = np.stack([d["px"], d["py"], d["pz"]], 1)
+    E = np.stack([d["ex"], d["ey"], d["ez"]], 1)
+    B = np.stack([d["bx"], d["by"], d["bz"]], 1)
+    p2 = np.sum(p * p, 1)
+    en = np.sqrt(p2) if photon else np.sqrt(1.0 + p2)
+    f = en[:, None] * E + np.cross(p, B)
+    s = np.sum(f * f, 1) - np.sum(p * E, 1) ** 2
+    return np.sqrt(np.maximum(s, 0.0))
+
+
+def longrun_leg(api, tabs, ws, rank, steps=1000, chunk=100, n=1_000_000, extra=4_000_000):
+    """The full QS + BW workload over many steps: 1e6 electrons + 1e6 photons,
+    §4 momenta, Gaussian field components rescaled per particle so that chi is
+    log-uniform in [1e-3, 1e2], tables 256 / 256x256, dt = 10, 1000 steps,
+    secondaries appended to buffers of 4e6 per species; FP32 and FP64.  One
+    patch through qed_substep_batched, 100 steps per CUDA graph (device step
+    counter), the particle-steps counted on the device (QED_STAT_EVOLVED)."""
+    import torch
+
+    from paper_2110_00256_gb300 import workloads
+    host = {}
+    for k, seed, off in (("electrons", 101, 0), ("photons", 102, 10 ** 12)):
+        d = workloads.gaussian_fields(n, seed + 1000 * rank, 1e-3, 1e2, id_offset=off + rank * 10 ** 10)
+        d = workloads.rescale_fields(d, chi_for_inputs(d, k == "photons"))
+        d.pop("chi_target")
+        host[k] = d
+    out = {}
+    for name, prec in (("fp32", api.QED_F32), ("fp64", api.QED_F64)):
+        patch = {"electrons": api.SpeciesBuffers(n + extra, prec).set(host["electrons"]),
+                 "positrons": api.SpeciesBuffers(extra, prec),
+                 "photons": api.SpeciesBuffers(n + extra, prec).set(host["photons"])}
+        patch["fire"] = [api.FireBuffers(patch[k].capacity) for k in ("electrons", "positrons", "photons")]
+        b = api.Batch([patch], prec)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):  # dt = 0: loads the kernels, changes no particle
+            api.qed_substep_batched(tabs, b, 0.0, SEED, 0, api.make_opts(), stream=stream)
+        stats = api.Stats()
+        d_step = torch.zeros(1, dtype=torch.int64, device="cuda")
+        opts = api.make_opts(stats=stats, d_step=d_step)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(chunk):
+                    api.qed_substep_batched(tabs, b, DT, SEED, 0, opts, stream=stream)
+        d_step.zero_()
+        stats.t.zero_()
+        n0 = sum(int(patch[k].count.item()) for k in ("electrons", "positrons", "photons"))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps // chunk):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(ws, e0.elapsed_time(e1))
+        st = stats.as_dict()
+        n1 = sum(int(patch[k].count.item()) for k in ("electrons", "positrons", "photons"))
+        out[name] = {"value": sum_over_ranks(ws, st["evolved"]) / (ms * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms / steps, "steps": steps, "particles_start": n0, "particles_end": n1,
+                     "qs_events": st["qs_events"], "bw_events": st["bw_events"], "pairs": st["pairs"],
+                     "dropped_capacity": st["dropped_capacity"], "wait_timeout": st["wait_timeout"]}
+        del g, b, patch
+        torch.cuda.empty_cache()
+    out["workload"] = ("1e6 e- + 1e6 photons, p from §4, Gaussian E, B rescaled so chi is log-uniform in "
+                       "[1e-3, 1e2], tables 256 / 256x256, dt = 10, 1000 steps, 4e6 secondaries per species")
+    return out
+
+
 def schwinger_leg(api, ws):
     """Schwinger pairs per cell (qed_schwinger_pairs) on 1e8 FP32 cells: fields
     of PIC strength (components N(0, 1e-3) E_s: the rate underflows, the FP32
@@ -684,6 +760,9 @@ def gpu_main(args):
 
     if not args.no_schwinger:
         result.setdefault("paths", {})["schwinger"] = schwinger_leg(api, ws)
+
+    if not args.no_longrun:
+        result.setdefault("paths", {})["full_qs_bw_1000_steps"] = longrun_leg(api, tabs, ws, rank)
 
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

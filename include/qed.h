@@ -114,9 +114,14 @@ enum {
     QED_STAT_SCHWINGER_PAIRS = 10,   /* pairs made by qed_schwinger_pairs                  */
     QED_STAT_EVOLVED = 11,           /* particles the batched calls (qed_substep_batched,
                                         qed_push_substep_batched) evolved: each step adds
-                                        the live count of every species of every patch, so
-                                        the sum over steps is the particle-steps done     */
-    QED_STAT_COUNT = 12
+                                        the live count of every species of every patch,
+                                        less the photons that pair production removed and
+                                        qed_compact_species has not yet dropped
+                                        (QED_STAT_PAIRS - QED_STAT_COMPACTED of the same
+                                        array), so the sum over steps is the particle-steps
+                                        done                                              */
+    QED_STAT_COMPACTED = 12,         /* removed particles dropped by qed_compact_species    */
+    QED_STAT_COUNT = 13
 };
 
 typedef struct {
@@ -140,6 +145,14 @@ typedef struct {
                                 nor emit (the cut-off a PIC code applies to photon emission,
                                 §5); 0 = off                                                  */
     double bw_chi_cut;       /* the same for photons and pair production; 0 = off           */
+    int64_t wait_limit_cycles; /* limit, in SM clock cycles, of the waits between the producer
+                                warp and the consumer warps of the bulk-copy evolution (single
+                                and batched); 0 = the default of ~1 s.  A wait that runs out
+                                ends the CTA's work early (its particles are not evolved),
+                                counts QED_STAT_WAIT_TIMEOUT and sets QED_EW_WAIT_TIMEOUT; the
+                                producer still waits, with the full limit, for every copy it
+                                issued before the CTA exits.  Small values only serve to test
+                                that path                                                    */
 } qed_substep_opts;
 
 /* How qed_substep's evolution reads the particle arrays.  DIRECT: every thread
@@ -161,6 +174,25 @@ enum { QED_EVOLVE_DEFAULT = 0, QED_EVOLVE_DIRECT = 1, QED_EVOLVE_BULK = 2 };
 /* ------------------------------------------------------------------------- */
 const char *qed_last_error_message(void);
 const char *qed_version(void);
+
+/* Device error word.  The per-step calls only enqueue work, so what goes wrong
+ * on the device cannot be their return value: their kernels OR these bits into
+ * a word that the library keeps on every device, whether or not the caller
+ * passed a statistics array (the QED_STAT_* counters give the counts). */
+enum {
+    QED_EW_WAIT_TIMEOUT = 1u,  /* a bounded wait gave up (results of that launch incomplete) */
+    QED_EW_NONFINITE = 2u,     /* non-finite chi or optical depth (the particle never fires) */
+    QED_EW_CAPACITY = 4u,      /* an event was not executed: a destination species was full  */
+    QED_EW_FIRE_OVERFLOW = 8u  /* firing particles beyond a firing list's capacity            */
+};
+/* Synchronise `stream`, then read the current device's error word into
+ * *word_out (may be NULL) and clear it if `clear` != 0.  Returns QED_ERR_TIMEOUT
+ * if QED_EW_WAIT_TIMEOUT is set, else QED_ERR_CAPACITY for QED_EW_CAPACITY or
+ * QED_EW_FIRE_OVERFLOW, else QED_ERR_NUMERIC for QED_EW_NONFINITE, else QED_OK
+ * (QED_ERR_CUDA if the stream itself failed).  Not for use inside a stream
+ * capture (it synchronises).  The word covers every call on the device since it
+ * was last cleared, from any stream or thread. */
+qed_status qed_device_status(void *stream, uint32_t *word_out, int32_t clear);
 
 /* ------------------------------------------------------------------------- */
 /* units (§3.3: one normalised system inside, conversions at the boundary)    */
@@ -281,6 +313,36 @@ qed_status qed_substep(const qed_tables *t, const qed_species *electrons,
                        const qed_species *positrons, const qed_species *photons, double dt,
                        uint64_t seed, int64_t step, const qed_substep_opts *opts,
                        qed_precision prec, const qed_fire_list *fire, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* species diagnostics and upkeep                                             */
+/* ------------------------------------------------------------------------- */
+/* Energy of a species (§2.1, §2.2: photon emission conserves gamma + gamma_g,
+ * pair production gamma_+ + gamma_- = gamma_g, so the sum over the three
+ * species is invariant under the substep).  Adds sum_i w_i E_i over particles
+ * [0, *d_count) to d_out[0] and the number of particles with nonzero weight to
+ * d_out[1] (device double[2], accumulated, never reset by the library), with
+ * E = gamma = sqrt(1 + p^2) for leptons (photon == 0) and E = |p| for photons
+ * (photon != 0), in m_e c^2; removed particles (weight 0) add nothing.  FP64
+ * sums at either precision; one launch, stream-ordered, graph-capturable. */
+qed_status qed_species_energy(const qed_species *sp, qed_precision prec, int32_t photon, double *d_out,
+                              void *stream);
+
+/* Drop the removed particles of `sp` -- weight 0 and optical depth +inf, the
+ * mark that pair production leaves on a decayed photon (§3.1) -- so that they
+ * are no longer read every step.  With n = *d_count, r of them removed and
+ * n' = n - r: the live particles at [n', n) move into the removed slots in
+ * [0, n'), every array together (p, E, B, tau, tau_c, weight, id, and x, y, z
+ * when present), k-th live particle of the tail into the k-th removed slot of the
+ * head; then *d_count = n'.  The order of the particles is not kept (every
+ * random draw is keyed by id, so the physics does not depend on it).  d_work:
+ * device int64 scratch of at least QED_COMPACT_WORK(sp->capacity) entries,
+ * owned by the caller, free again when the call's work on `stream` is done.
+ * d_stats (may be NULL): QED_STAT_COMPACTED grows by r.  Four launches, no
+ * host synchronisation, graph-capturable. */
+#define QED_COMPACT_WORK(cap) (2 * (int64_t)(cap) + ((int64_t)(cap) + 2047) / 2048 + 8)
+qed_status qed_compact_species(const qed_species *sp, qed_precision prec, int64_t *d_work, int64_t work_capacity,
+                               int64_t *d_stats, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Schwinger pair production (§2.3)                                          */

@@ -23,7 +23,12 @@ QED_MAX_TABLE_N = 1024
 (QED_STAT_QS_EVENTS, QED_STAT_BW_EVENTS, QED_STAT_PHOTONS_KEPT, QED_STAT_PHOTONS_DISCARDED,
  QED_STAT_PAIRS, QED_STAT_BW_NO_PAIR, QED_STAT_DROPPED_CAPACITY, QED_STAT_NONFINITE,
  QED_STAT_FIRE_OVERFLOW, QED_STAT_WAIT_TIMEOUT, QED_STAT_SCHWINGER_PAIRS, QED_STAT_EVOLVED,
- QED_STAT_COUNT) = range(13)
+ QED_STAT_COMPACTED, QED_STAT_COUNT) = range(14)
+QED_EW_WAIT_TIMEOUT, QED_EW_NONFINITE, QED_EW_CAPACITY, QED_EW_FIRE_OVERFLOW = 1, 2, 4, 8
+
+
+def QED_COMPACT_WORK(cap: int) -> int:
+    return 2 * int(cap) + (int(cap) + 2047) // 2048 + 8
 
 
 class QedError(RuntimeError):
@@ -74,7 +79,8 @@ class SubstepOpts(C.Structure):
     _fields_ = [("photon_threshold", C.c_double), ("sampler", C.c_int32), ("mlp", C.c_void_p),
                 ("d_stats", C.c_void_p), ("evolve_begin", C.c_void_p), ("evolve_end", C.c_void_p),
                 ("d_step", C.c_void_p), ("evolve_threads", C.c_int32), ("evolve_ctas_per_sm", C.c_int32),
-                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double)]
+                ("evolve_pipeline", C.c_int32), ("qs_chi_cut", C.c_double), ("bw_chi_cut", C.c_double),
+                ("wait_limit_cycles", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -126,6 +132,9 @@ SIGNATURES = {
     "qed_mlp_gradients": (_S, [_P, _S, _P, _P, _P, _I64, _P, _P, _P]),
     "qed_mlp_sample": (_S, [_P, _S, _P, _P, _I64, _P, _P]),
     "qed_table_sample": (_S, [_P, _S, _S, _P, _P, _I64, _P, _P]),
+    "qed_device_status": (_S, [_P, C.POINTER(C.c_uint32), C.c_int32]),
+    "qed_species_energy": (_S, [C.POINTER(Species), _S, C.c_int32, _P, _P]),
+    "qed_compact_species": (_S, [C.POINTER(Species), _S, _P, _I64, _P, _P]),
 }
 QED_MLP_PARAMS = 4417
 QED_MAX_PATCHES = 1024

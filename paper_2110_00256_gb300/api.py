@@ -25,7 +25,7 @@ __all__ = [
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
     "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields", "qed_push_substep_batched",
     "qed_schwinger_pairs",
-    "qed_push_batched",
+    "qed_push_batched", "qed_device_status", "qed_species_energy", "qed_compact_species", "CompactWork",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -190,7 +190,8 @@ class Stats:
     """Device counters (QED_STAT_*)."""
 
     NAMES = ("qs_events", "bw_events", "photons_kept", "photons_discarded", "pairs", "bw_no_pair",
-             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout", "schwinger_pairs", "evolved")
+             "dropped_capacity", "nonfinite", "fire_overflow", "wait_timeout", "schwinger_pairs", "evolved",
+             "compacted")
 
     def __init__(self, device="cuda"):
         self.t = torch.zeros(QED_STAT_COUNT, dtype=torch.int64, device=device)
@@ -424,8 +425,10 @@ def qed_tune_evolve(t: Tables, b: Batch, stream=None) -> dict:
 
 def make_opts(photon_threshold=0.0, stats: Stats | None = None, mlp: "Mlp | None" = None,
               d_step: torch.Tensor | None = None, evolve_threads: int = 0, evolve_ctas_per_sm: int = 0,
-              evolve_pipeline: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0) -> SubstepOpts:
+              evolve_pipeline: int = 0, qs_chi_cut: float = 0.0, bw_chi_cut: float = 0.0,
+              wait_limit_cycles: int = 0) -> SubstepOpts:
     o = _opts(photon_threshold, stats, qs_chi_cut, bw_chi_cut)
+    o.wait_limit_cycles = int(wait_limit_cycles)
     if mlp is not None:
         o.sampler = 1
         o.mlp = mlp.handle.value
@@ -459,3 +462,38 @@ def qed_push_batched(b: Batch, wave, t0: float, dt: float, step: int = 0, d_step
                      stream=None):
     check(lib().qed_push_batched(b.handle, C.byref(wave), float(t0), float(dt), int(step),
                                  d_step.data_ptr() if d_step is not None else None, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------
+# device error word, species diagnostics and upkeep
+# ---------------------------------------------------------------------------------------
+def qed_device_status(stream=None, clear: bool = True) -> tuple:
+    """Synchronise the stream and read (and by default clear) the device error
+    word; returns (status, word) without raising (include/qed.h)."""
+    w = C.c_uint32(0)
+    st = lib().qed_device_status(_stream(stream), C.byref(w), 1 if clear else 0)
+    return st, w.value
+
+
+def qed_species_energy(sp: SpeciesBuffers, photon: bool, out: torch.Tensor | None = None, stream=None):
+    """Adds (sum of weight x energy, number with nonzero weight) of the species
+    to the device FP64 pair `out` (zeros if None) and returns it."""
+    if out is None:
+        out = torch.zeros(2, dtype=torch.float64, device=sp.device)
+    s = sp.struct()
+    check(lib().qed_species_energy(C.byref(s), sp.prec, 1 if photon else 0, out.data_ptr(), _stream(stream)))
+    return out
+
+
+class CompactWork:
+    """Device scratch of qed_compact_species for species of up to `capacity` particles."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        self.capacity = int(capacity)
+        self.t = torch.empty(_lib.QED_COMPACT_WORK(capacity), dtype=torch.int64, device=device)
+
+
+def qed_compact_species(sp: SpeciesBuffers, work: CompactWork, stats: Stats | None = None, stream=None):
+    s = sp.struct()
+    check(lib().qed_compact_species(C.byref(s), sp.prec, work.t.data_ptr(), int(work.t.numel()),
+                                    stats.t.data_ptr() if stats is not None else None, _stream(stream)))

@@ -50,7 +50,9 @@ namespace qed {
 
 // one CTA of 256: zero the n firing counts; with stats, add the live counts of
 // the species (the first three of every six clamp entries), clamped as the
-// evolution clamps them, to QED_STAT_EVOLVED: the particles this step evolves
+// evolution clamps them, to QED_STAT_EVOLVED: the particles this step evolves,
+// less the photons removed by pair production that are still in the arrays
+// (QED_STAT_PAIRS - QED_STAT_COMPACTED: they are read, but not evolved)
 __global__ void __launch_bounds__(256) zero_counts_kernel(int64_t *const *p, int n, const ClampEntry *e,
                                                           int n_patches, long long *stats)
 {
@@ -70,7 +72,9 @@ __global__ void __launch_bounds__(256) zero_counts_kernel(int64_t *const *p, int
     if (threadIdx.x == 0) {
         long long t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
-        atomicAdd((unsigned long long *)(stats + QED_STAT_EVOLVED), (unsigned long long)t);
+        long long removed = stats[QED_STAT_PAIRS] - stats[QED_STAT_COMPACTED];
+        removed = removed < 0 ? 0 : (removed > t ? t : removed);
+        atomicAdd((unsigned long long *)(stats + QED_STAT_EVOLVED), (unsigned long long)(t - removed));
     }
 }
 
@@ -221,25 +225,28 @@ __device__ __forceinline__ const float *seg_stream(const EvolveSeg<float> &g, in
     }
 }
 
-__device__ __forceinline__ bool seg_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool seg_wait(uint64_t *bar, uint32_t parity, volatile int *abort, long long limit)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
-        if (*abort || clock64() - t0 > kWaitCycles) return false;
+        if (*abort || clock64() - t0 > limit) return false;
     }
     return true;
 }
 
 __device__ __forceinline__ void seg_give_up(int *abort, long long *stats)
 {
-    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    if (atomicExch(abort, 1) == 0) {
+        note_error(QED_EW_WAIT_TIMEOUT);
+        if (stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    }
 }
 
 template <int CW, int S>
 __global__ void __launch_bounds__((CW + 1) * 32, 1)
     evolve_seg_bulk_kernel(const EvolveSeg<float> *__restrict__ segs, int n_seg, TablesView<float> tab, float dt,
-                           float cut_qs, float cut_bw, long long *stats, int dry)
+                           float cut_qs, float cut_bw, long long *stats, int dry, long long wait_cycles)
 {
     constexpr int THREADS = (CW + 1) * 32;
     constexpr int TP = CW * 32 * 4;
@@ -267,6 +274,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
     const long long total = tile_prefix<float, THREADS>(segs, n_seg, TP, s_end, s_n, s_warp);  // ends with a barrier
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort = &s_abort;
+    // the producer/consumer hand-offs use the caller's limit; the final wait for
+    // the copies in flight always the full one
+    const long long limit = wait_cycles > 0 ? wait_cycles : kWaitCycles;
 
     if (warp == CW) {  // producer
         const uint64_t pol = l2_evict_first();
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
             const uint32_t ph = (uint32_t)(k / S) & 1u;
             while (s_end[s] <= t) ++s;  // tiles ascend: the segment only moves forward
             const int64_t i0 = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
-            if (!__all_sync(0xffffffffu, seg_wait(&s_empty[st], ph ^ 1u, abort))) {
+            if (!__all_sync(0xffffffffu, seg_wait(&s_empty[st], ph ^ 1u, abort, limit))) {
                 if (lane == 0) seg_give_up(&s_abort, stats);
                 break;
             }
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         const int64_t n = s_n[s];
         const int64_t base = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
         const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
-        if (!__all_sync(0xffffffffu, seg_wait(&s_full[st], ph, abort))) {
+        if (!__all_sync(0xffffffffu, seg_wait(&s_full[st], ph, abort, limit))) {
             if (lane == 0) seg_give_up(&s_abort, stats);
             break;
         }
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         evolve_regs<float, 4>(sg, n, i0, full4, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, tab, dt,
                               sg.proc == QED_PROC_QS ? cut_qs : cut_bw, stats, dry, bad);
     }
-    if (stats && !dry) warp_count(stats + QED_STAT_NONFINITE, bad);
+    if (!dry) warp_count_err(stats ? stats + QED_STAT_NONFINITE : nullptr, bad, QED_EW_NONFINITE);
 }
 
 // 15 consumer warps + the producer (16 warps, one CTA per SM), 2 stages, as the single-call default
@@ -357,7 +367,7 @@ constexpr int kSegBulkCW = 15, kSegBulkS = 2;
 
 static qed_status launch_evolve_seg_bulk(const EvolveSeg<float> *segs, int n_seg, const TablesView<float> &tab,
                                          float dt, float cut_qs, float cut_bw, long long *stats, int dry,
-                                         cudaStream_t st)
+                                         long long wait_cycles, cudaStream_t st)
 {
     constexpr size_t stage = (size_t)kSegBulkS * kSegArrays * kSegBulkCW * 32 * 4 * sizeof(float);
     const size_t dyn = stage + (size_t)n_seg * 2 * sizeof(long long);
@@ -368,7 +378,8 @@ static qed_status launch_evolve_seg_bulk(const EvolveSeg<float> *segs, int n_seg
                                           (int)(stage + 3 * QED_MAX_PATCHES * 2 * sizeof(long long))));
         attr = true;
     }
-    k<<<sm_count(), (kSegBulkCW + 1) * 32, dyn, st>>>(segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry);
+    k<<<sm_count(), (kSegBulkCW + 1) * 32, dyn, st>>>(segs, n_seg, tab, dt, cut_qs, cut_bw, stats, dry,
+                                                       wait_cycles);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }
@@ -540,7 +551,7 @@ static qed_status substep_batched_impl(const qed_tables *t, const qed_batch *b, 
                                   store_fields, b->push_vec, st);
     } else if constexpr (sizeof(T) == 4) {
         s = bulk ? launch_evolve_seg_bulk((const EvolveSeg<float> *)b->d_evolve, 3 * n, make_view<float>(t),
-                                          (float)dt, cut_qs, cut_bw, stats, 0, st)
+                                          (float)dt, cut_qs, cut_bw, stats, 0, o ? o->wait_limit_cycles : 0, st)
                  : launch_evolve_segments<T>((const EvolveSeg<T> *)b->d_evolve, 3 * n, make_view<T>(t), (T)dt,
                                              cut_qs, cut_bw, stats, 0, b->vec, threads, ctas, st);
     } else {
@@ -676,7 +687,7 @@ extern "C" qed_status qed_tune_evolve(const qed_tables *t, qed_batch *b, int32_t
         for (int rep = 0; rep < 4 && s == QED_OK; ++rep) {
             cudaEventRecord(e0, st);
             s = launch_evolve_seg_bulk((const EvolveSeg<float> *)b->d_evolve, 3 * b->n_patches, make_view<float>(t),
-                                       0.f, 0.f, 0.f, nullptr, 1, st);
+                                       0.f, 0.f, 0.f, nullptr, 1, 0, st);
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             float ms = 0.f;

@@ -46,7 +46,49 @@ qed_status check_species(const qed_species *s, const char *name, qed_precision p
     return QED_OK;
 }
 
+// The error words of all translation units, registered during static
+// initialisation (a function-local table, so the order of initialisation of
+// the translation units does not matter).
+struct ErrWordRegistry {
+    ErrWordIO fn[64];
+    int n = 0;
+};
+
+static ErrWordRegistry &err_registry()
+{
+    static ErrWordRegistry r;
+    return r;
+}
+
+int register_err_word(ErrWordIO f)
+{
+    ErrWordRegistry &r = err_registry();
+    if (r.n < 64) r.fn[r.n++] = f;
+    return r.n;
+}
+
 }  // namespace qed
+
+extern "C" qed_status qed_device_status(void *stream, uint32_t *word_out, int32_t clear)
+{
+    using namespace qed;
+    clear_error();
+    QED_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    unsigned w = 0;
+    ErrWordRegistry &r = err_registry();
+    for (int i = 0; i < r.n; ++i) {
+        unsigned v = 0;
+        QED_CUDA_TRY(r.fn[i](&v, clear != 0));
+        w |= v;
+    }
+    if (word_out) *word_out = w;
+    if (w & QED_EW_WAIT_TIMEOUT)
+        QED_FAIL(QED_ERR_TIMEOUT, "a bounded wait gave up on the device (error word 0x%x)", w);
+    if (w & (QED_EW_CAPACITY | QED_EW_FIRE_OVERFLOW))
+        QED_FAIL(QED_ERR_CAPACITY, "events were left unexecuted for lack of room (error word 0x%x)", w);
+    if (w & QED_EW_NONFINITE) QED_FAIL(QED_ERR_NUMERIC, "non-finite chi or optical depth seen (error word 0x%x)", w);
+    return QED_OK;
+}
 
 extern "C" const char *qed_last_error_message(void) { return qed::g_err; }
 

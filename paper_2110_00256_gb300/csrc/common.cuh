@@ -152,6 +152,37 @@ __device__ __forceinline__ void warp_count(long long *ctr, int v)
     if (lane_id() == 0 && s) atomicAdd((unsigned long long *)ctr, (unsigned long long)s);
 }
 
+// ---------------------------------------------------------------------------
+// device error word (qed_device_status): every translation unit keeps its own
+// word, which its kernels OR their QED_EW_* bits into whether or not the caller
+// passed a statistics array; a host-side registry reads (and clears) all of them.
+// ---------------------------------------------------------------------------
+static __device__ unsigned int g_err_word;
+
+__device__ __forceinline__ void note_error(unsigned bit) { atomicOr(&g_err_word, bit); }
+
+// per-lane counts into a statistic (if any) and, where a lane counted, the error bit
+__device__ __forceinline__ void warp_count_err(long long *ctr, int v, unsigned bit)
+{
+    if (v) note_error(bit);
+    warp_count(ctr, v);
+}
+
+using ErrWordIO = cudaError_t (*)(unsigned *out, bool clear);
+int register_err_word(ErrWordIO f);
+
+static cudaError_t err_word_io(unsigned *out, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_err_word, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned z = 0;
+        e = cudaMemcpyToSymbol(g_err_word, &z, sizeof(unsigned));
+    }
+    return e;
+}
+
+[[maybe_unused]] static const int g_err_word_registered = register_err_word(&err_word_io);
+
 }  // namespace qed
 
 // opaque handle definition shared by the .cu files

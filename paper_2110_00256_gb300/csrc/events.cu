@@ -257,6 +257,7 @@ static qed_status substep_impl(const qed_tables *t, const qed_species *e, const 
     a.stats = o ? (long long *)o->d_stats : nullptr;
     a.chi_cut[QED_PROC_QS] = o ? (T)o->qs_chi_cut : T(0);
     a.chi_cut[QED_PROC_BW] = o ? (T)o->bw_chi_cut : T(0);
+    a.wait_cycles = o ? o->wait_limit_cycles : 0;
     bool vec = fill_seg<T>(a.seg[0], e, QED_PROC_QS, &fire[0]);
     vec = fill_seg<T>(a.seg[1], p, QED_PROC_QS, &fire[1]) && vec;
     vec = fill_seg<T>(a.seg[2], g, QED_PROC_BW, &fire[2]) && vec;

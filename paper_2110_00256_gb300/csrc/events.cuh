@@ -238,6 +238,7 @@ __device__ __forceinline__ void bw_event_chunk(const EventSeg<T> &g, const Event
 
 __device__ __forceinline__ void flush_counts(long long *stats, const EventCounts &k, bool qs)
 {
+    if (k.drop) note_error(QED_EW_CAPACITY);
     if (!stats) return;
     if (qs) {
         warp_count(stats + QED_STAT_QS_EVENTS, k.exec);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kEvolveThreads, MINB)
         evolve_tile<T, VEC, kEvolveThreads>(a.seg[s], s_n[s], t - (s ? s_end[s - 1] : 0), s_qs, s_bw, a.tab, a.dt,
                                             a.chi_cut[a.seg[s].proc], a.stats, 0, bad);
     }
-    if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
+    warp_count_err(a.stats ? a.stats + QED_STAT_NONFINITE : nullptr, bad, QED_EW_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -114,20 +114,23 @@ __global__ void __launch_bounds__(kEvolveThreads, MINB)
 // ---------------------------------------------------------------------------
 constexpr int kBulkArrays = 11;
 
-// bounded wait that also gives up as soon as another warp has given up
-__device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+// bounded wait (limit cycles) that also gives up as soon as another warp has given up
+__device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity, volatile int *abort, long long limit)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
-        if (*abort || clock64() - t0 > kWaitCycles) return false;
+        if (*abort || clock64() - t0 > limit) return false;
     }
     return true;
 }
 
 __device__ __forceinline__ void bulk_give_up(int *abort, long long *stats)
 {
-    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    if (atomicExch(abort, 1) == 0) {
+        note_error(QED_EW_WAIT_TIMEOUT);
+        if (stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    }
 }
 
 template <int CW, int S>
@@ -169,6 +172,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
     const long long total = a.n_seg ? s_end[a.n_seg - 1] : 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort = &s_abort;
+    // the producer/consumer hand-offs use the caller's limit; the final wait for
+    // the copies in flight (below) always the full one
+    const long long limit = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
 
     if (warp == CW) {  // producer
         const uint64_t pol = l2_evict_first();
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
             int s = 0;
             while (t >= s_end[s]) ++s;
             const int64_t i0 = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
-            const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_empty[st], ph ^ 1u, abort));
+            const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_empty[st], ph ^ 1u, abort, limit));
             if (!ok) {
                 if (lane == 0) bulk_give_up(&s_abort, a.stats);
                 break;
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         const int64_t n = s_n[s];
         const int64_t base = (t - (s ? s_end[s - 1] : 0)) * (int64_t)TP;
         const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
-        const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_full[st], ph, abort));
+        const bool ok = __all_sync(0xffffffffu, bulk_wait(&s_full[st], ph, abort, limit));
         if (!ok) {
             if (lane == 0) bulk_give_up(&s_abort, a.stats);
             break;
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, MINB)
         evolve_regs<float, 4>(sg, n, i0, full4, px, py, pz, ex, ey, ez, bx, by, bz, tau, tc, s_qs, s_bw, a.tab,
                               a.dt, a.chi_cut[sg.proc], a.stats, 0, bad);
     }
-    if (a.stats) warp_count(a.stats + QED_STAT_NONFINITE, bad);
+    warp_count_err(a.stats ? a.stats + QED_STAT_NONFINITE : nullptr, bad, QED_EW_NONFINITE);
 }
 
 template <int CW, int S, int MINB, int MAXSEG>
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS)
         evolve_tile<T, VEC, THREADS>(sg, s_n[lo], t - (lo ? s_end[lo - 1] : 0), s_qs, s_bw, tab, dt,
                                      sg.proc == QED_PROC_QS ? cut_qs : cut_bw, stats, dry, bad);
     }
-    if (stats && !dry) warp_count(stats + QED_STAT_NONFINITE, bad);
+    if (!dry) warp_count_err(stats ? stats + QED_STAT_NONFINITE : nullptr, bad, QED_EW_NONFINITE);
 }
 
 template <typename T, int THREADS>

@@ -30,6 +30,7 @@ struct EvolveArgs {
     EvolveSeg<T> seg[MAXSEG];
     TablesView<T> tab;
     long long *stats;
+    long long wait_cycles;  // limit of the producer/consumer waits of the bulk-copy form (0: kWaitCycles)
     T dt;
     T chi_cut[2];  // per process (QED_PROC_QS, QED_PROC_BW): below it the rate is taken as zero
     int n_seg;

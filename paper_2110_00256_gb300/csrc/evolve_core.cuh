@@ -123,7 +123,7 @@ __device__ __forceinline__ void compact_fire(const EvolveSeg<T> &sg, int64_t i0,
             ++pos;
         }
     }
-    if (stats) warp_count(stats + QED_STAT_FIRE_OVERFLOW, over);
+    warp_count_err(stats ? stats + QED_STAT_FIRE_OVERFLOW : nullptr, over, QED_EW_FIRE_OVERFLOW);
 }
 
 // Evaluate, store and compact VEC particles [i0, i0 + VEC) of segment `sg`

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2)
         if constexpr (sizeof(T) == 4) store_live<T, VEC>(sg.tau_c, i0, n, full, tc);
         compact_fire<T, VEC>(sg, i0, fire, chi, cnt, stats);
     }
-    if (stats) warp_count(stats + QED_STAT_NONFINITE, bad);
+    warp_count_err(stats ? stats + QED_STAT_NONFINITE : nullptr, bad, QED_EW_NONFINITE);
 }
 
 template <typename T, int VEC>

@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, co
         parity ^= 1u;
         if (!done) {
             S.fail[grp] = 1;  // seen by the whole group after its next barrier
+            note_error(QED_EW_WAIT_TIMEOUT);
             if (valid) xi[i] = __longlong_as_double(0x7ff8000000000000LL);
             continue;
         }

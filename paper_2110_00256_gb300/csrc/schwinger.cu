@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(256, 3) schwinger_kernel(CellsView<T> c, doubl
         if (__any_sync(0xffffffffu, tot > 0))
             make_pairs<T, VEC>(c0, c, dv, dt, weight, seed, step, ln_scale, e, p, made, dropped);
     }
+    if (dropped) note_error(QED_EW_CAPACITY);
     if (stats) {
         warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
         warp_count64(stats + QED_STAT_DROPPED_CAPACITY, dropped);
@@ -288,7 +289,10 @@ __device__ __forceinline__ bool cell_wait(uint64_t *bar, uint32_t parity, volati
 
 __device__ __forceinline__ void cell_give_up(int *abort, long long *stats)
 {
-    if (atomicExch(abort, 1) == 0 && stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    if (atomicExch(abort, 1) == 0) {
+        note_error(QED_EW_WAIT_TIMEOUT);
+        if (stats) atomicAdd((unsigned long long *)(stats + QED_STAT_WAIT_TIMEOUT), 1ull);
+    }
 }
 
 template <int CW, int S>
@@ -378,6 +382,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         if (__any_sync(0xffffffffu, tot > 0))
             make_pairs<float, 4>(c0, c, dv, dt, weight, seed, step, ln_scale, e, p, made, dropped);
     }
+    if (dropped) note_error(QED_EW_CAPACITY);
     if (stats) {
         warp_count64(stats + QED_STAT_SCHWINGER_PAIRS, made);
         warp_count64(stats + QED_STAT_DROPPED_CAPACITY, dropped);

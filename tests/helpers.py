@@ -208,3 +208,43 @@ def check_substep_fp32(ot, host, got, fire_lists, dt, seed, step, rtol_r=1e-5):
                 assert abs(rr - rs) <= rtol_r * rs + 1e-12, (name, pid, rs, rr)
                 assert gw[j] == 0 and np.isinf(gt[j])
     return report
+
+
+def margin_ids(ot, host64, dt, tol, seed, step, cuts=(0.0, 0.0)):
+    """ids of particles whose decision lies within the error bound (of the
+    firing test or of a chi cut-off), and their children."""
+    out = set()
+    for k, proc in (("electrons", 0), ("positrons", 0), ("photons", 1)):
+        tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt, cuts[proc])
+        b = tau_bound(ot, proc, host64[k], chi, rate, dt, tol)
+        near_cut = np.abs(chi - cuts[proc]) <= 1e-9 * cuts[proc]
+        for pid in host64[k]["id"][(np.abs(tn) <= b) | near_cut].tolist():
+            out.add(pid)
+            out |= set(oracle.child_ids(seed, pid, step))
+    return out
+
+
+def compare_states(got, ref, prec_f32, tol, exclude=frozenset()):
+    worst = {}
+    for k in ("electrons", "positrons", "photons"):
+        g, r = sort_by_id(got[k]), sort_by_id({kk: ref[k][kk] for kk in got[k]})
+        if exclude:
+            keep_g = ~np.isin(g["id"], list(exclude))
+            keep_r = ~np.isin(r["id"], list(exclude))
+            g = {kk: v[keep_g] for kk, v in g.items()}
+            r = {kk: v[keep_r] for kk, v in r.items()}
+        assert np.array_equal(g["id"], r["id"]), f"{k}: id sets differ ({len(g['id'])} vs {len(r['id'])})"
+        gt = tau_eff(g, prec_f32)
+        fin = np.isfinite(r["tau"])
+        assert np.array_equal(np.isfinite(gt), fin), f"{k}: removed-particle mask"
+        pm = np.sqrt(r["px"] ** 2 + r["py"] ** 2 + r["pz"] ** 2)
+        e = 0.0
+        for c in ("px", "py", "pz"):
+            e = max(e, float(np.max(np.abs(g[c] - r[c]) / np.maximum(pm, 1e-300), initial=0)))
+        et = float(np.max(np.abs(gt[fin] - r["tau"][fin]) / np.maximum(np.abs(r["tau"][fin]), 1.0), initial=0))
+        for c in ("ex", "ey", "ez", "bx", "by", "bz", "weight"):
+            assert np.array_equal(g[c].astype(np.float64), r[c]), f"{k}: {c} copied exactly"
+        worst[k] = (e, et)
+        assert e <= tol, f"{k}: momentum rel err {e:.3e}"
+        assert et <= tol, f"{k}: tau err {et:.3e}"
+    return worst

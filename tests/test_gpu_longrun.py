@@ -1,0 +1,262 @@
+"""The full QS + BW workload over many steps (§3, §4): 10^6 electrons and 10^6
+photons with momenta from the §4 benchmark distribution, Gaussian field
+components rescaled per particle so that chi is log-uniform in [1e-3, 1e2]
+(the rescaling chi is the oracle's), tables of 256 / 256x256, dt = 10,
+1000 steps, secondaries appended to preallocated buffers (capacity 4e6 per
+species), FP64 and FP32.
+
+Checks:
+* FP64 against the oracle element by element at the 1st, 10th and 100th step,
+  the oracle starting each time from the GPU's state before that step;
+* the oracle run for all 1000 steps on a 10^4-particle subsample (5000 of each
+  species, the same ids): every particle it ends with, and every descendant,
+  is found on the GPU (FP64) with the same state;
+* FP32 against FP64 on the GPU: the same random streams make the same events,
+  except where the FP32 rounding of the optical depth moves an event by one
+  step; the fraction of primaries whose history differs, the per-step and total
+  event counts, the chi distribution of the events and the secondaries' energy
+  spectra are compared with stated tolerances;
+* both precisions against the oracle's subsample statistically: events per
+  particle-step in 5 chi bins and the secondaries' spectra per primary, within
+  5 standard deviations of the counts (Poisson);
+* the total energy sum w E over the three species (qed_species_energy), per
+  step: conserved to 1e-12 (FP64) and 1e-7 (FP32) relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import as_f64, compare_states, gpu_tables, margin_ids
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SPECIES = ("electrons", "positrons", "photons")
+N = 1_000_000
+STEPS = 1000
+DT = 10.0
+SEED = 20211002
+EXTRA = 4_000_000
+SUB = 5000                      # oracle subsample: this many of each primary species
+CHI_EDGES = np.geomspace(1e-3, 1e2, 6)
+E_EDGES = np.geomspace(1e-2, 1e4, 25)
+PHOTON_ID0 = 10 ** 12
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2110_00256_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def setup(api, oracle_tables_256):
+    """Inputs (FP64 host arrays), the rescaling chi taken from the oracle."""
+    from paper_2110_00256_gb300 import workloads
+    ot = oracle_tables_256
+    host = {}
+    for k, proc, seed, off in (("electrons", 0, 101, 0), ("photons", 1, 102, PHOTON_ID0)):
+        d = workloads.gaussian_fields(N, seed, 1e-3, 1e2, id_offset=off)
+        chi = oracle.evolve(proc, ot, d, 0.0)[1]
+        d = workloads.rescale_fields(d, chi)
+        d.pop("chi_target")
+        host[k] = d
+    host["positrons"] = {k: v[:0].copy() for k, v in host["electrons"].items()}
+    return ot, gpu_tables(api, ot), host
+
+
+def _species(api, host, prec):
+    caps = {"electrons": N + EXTRA, "positrons": EXTRA, "photons": N + EXTRA}
+    bufs = {}
+    for k in SPECIES:
+        b = api.SpeciesBuffers(caps[k], prec)
+        if len(host[k]["px"]):
+            b.set(host[k])
+        bufs[k] = b
+    return bufs, [api.FireBuffers(bufs[k].capacity) for k in SPECIES]
+
+
+def _energy(api, bufs):
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for k in SPECIES:
+        api.qed_species_energy(bufs[k], k == "photons", out)
+    return out
+
+
+def _run(api, t, host, prec, ot=None, check_steps=()):
+    """1000 steps; per step: stats snapshot, energy, the firing chi; element-
+    by-element checks against the oracle at check_steps (FP64 only)."""
+    bufs, fire = _species(api, host, prec)
+    stats = api.Stats()
+    call = api.SubstepCall(t, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED, stats=stats)
+    hist = torch.zeros((STEPS, len(api.Stats.NAMES)), dtype=torch.int64, device="cuda")
+    energy = torch.zeros((STEPS + 1, 2), dtype=torch.float64, device="cuda")
+    energy[0] = _energy(api, bufs)
+    counts = np.zeros((STEPS, 3), dtype=np.int64)
+    fire_chi = {"qs": [], "bw": []}
+    checked = 0
+    for s in range(STEPS):
+        counts[s] = [bufs[k].n() for k in SPECIES]
+        pre = None
+        if s in check_steps:
+            pre = {k: bufs[k].to_host() for k in SPECIES}
+        call(s)
+        hist[s] = stats.t
+        energy[s + 1] = _energy(api, bufs)
+        for k, f in zip(SPECIES, fire):
+            m = f.n()
+            if m:
+                fire_chi["bw" if k == "photons" else "qs"].append(f.chi[:m].cpu().numpy())
+        if pre is not None:
+            torch.cuda.synchronize()
+            got = {k: bufs[k].to_host() for k in SPECIES}
+            h64 = {k: {c: v for c, v in pre[k].items()} for k in SPECIES}
+            ref = oracle.substep(ot, h64, dt=DT, seed=SEED, step=s)
+            excl = margin_ids(ot, h64, DT, 1e-12, SEED, s)
+            assert len(excl) <= 20
+            compare_states(got, ref, False, 1e-12, exclude=excl)
+            checked += 1
+    torch.cuda.synchronize()
+    assert checked == len(check_steps)
+    final = {k: bufs[k].to_host() for k in SPECIES}
+    per_step = np.diff(np.vstack([np.zeros((1, hist.shape[1]), dtype=np.int64), hist.cpu().numpy()]), axis=0)
+    return dict(final=final, per_step=per_step, stats=stats.as_dict(), energy=energy.cpu().numpy(),
+                counts=counts, fire_chi={k: np.concatenate(v) if v else np.zeros(0) for k, v in fire_chi.items()})
+
+
+def _oracle_subsample(ot, host):
+    from paper_2110_00256_gb300 import workloads
+    sub = {}
+    for k in ("electrons", "photons"):
+        idx = workloads.subsample_ids(N, SUB, 7 if k == "electrons" else 8)
+        sub[k] = {c: v[idx] for c, v in host[k].items()}
+    sub["positrons"] = {c: v[:0].copy() for c, v in host["electrons"].items()}
+    sp = {k: as_f64(v, np.float64) for k, v in sub.items()}
+    n_qs = n_bw = 0
+    ps = {"qs": 0, "bw": 0}
+    chi = {"qs": [], "bw": []}
+    for s in range(STEPS):
+        ps["qs"] += len(sp["electrons"]["px"]) + len(sp["positrons"]["px"])
+        ps["bw"] += len(sp["photons"]["px"])
+        out = oracle.substep(ot, sp, dt=DT, seed=SEED, step=s)
+        for k, key in (("electrons", "qs"), ("positrons", "qs"), ("photons", "bw")):
+            f = out["fire"][k]
+            chi[key].append(out["chi"][k][f])
+        n_qs += int(out["fire"]["electrons"].sum() + out["fire"]["positrons"].sum())
+        n_bw += int(out["fire"]["photons"].sum())
+        sp = {k: {c: out[k][c] for c in sp[k]} for k in SPECIES}
+    return dict(final=sp, n_qs=n_qs, n_bw=n_bw, ps=ps, fire_chi={k: np.concatenate(v) for k, v in chi.items()})
+
+
+def _by_id(d):
+    return {int(i): j for j, i in enumerate(d["id"])}
+
+
+def _is_primary(ids):
+    ids = np.asarray(ids, dtype=np.uint64)
+    return (ids < np.uint64(N)) | ((ids >= np.uint64(PHOTON_ID0)) & (ids < np.uint64(PHOTON_ID0 + N)))
+
+
+def _secondary_spectra(final):
+    """Energy histograms of the particles made during the run: photons by |p|,
+    pair leptons (electrons with non-primary ids, positrons) by gamma - 1."""
+    ph = final["photons"]
+    keep = (~_is_primary(ph["id"])) & (ph["weight"] > 0)
+    e_ph = np.sqrt(ph["px"].astype(np.float64) ** 2 + ph["py"] ** 2 + ph["pz"] ** 2)[keep]
+    lep = []
+    for k in ("electrons", "positrons"):
+        d = final[k]
+        m = ~_is_primary(d["id"])
+        p2 = d["px"].astype(np.float64) ** 2 + d["py"].astype(np.float64) ** 2 + d["pz"].astype(np.float64) ** 2
+        lep.append((p2 / (np.sqrt(1.0 + p2) + 1.0))[m])
+    return np.histogram(e_ph, E_EDGES)[0], np.histogram(np.concatenate(lep), E_EDGES)[0]
+
+
+def _poisson_close(a, na, b, nb, k=5.0):
+    """a / na and b / nb (counts over exposures) agree within k standard deviations."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    sig = np.sqrt((a + 1.0) / na ** 2 + (b + 1.0) / nb ** 2)
+    return np.abs(a / na - b / nb) <= k * sig
+
+
+def test_full_qs_bw_1000_steps(api, setup):
+    ot, t, host = setup
+    r64 = _run(api, t, host, api.QED_F64, ot, check_steps=(0, 9, 99))
+    r32 = _run(api, t, host, api.QED_F32)
+    orc = _oracle_subsample(ot, host)
+    for r in (r64, r32):
+        s = r["stats"]
+        assert s["dropped_capacity"] == 0 and s["fire_overflow"] == 0 and s["nonfinite"] == 0
+        assert s["wait_timeout"] == 0
+        assert s["qs_events"] > 100_000 and s["pairs"] > 20_000
+
+    # 1. the oracle's subsample, particle by particle, in the FP64 run
+    g = r64["final"]
+    gi = {k: _by_id(g[k]) for k in SPECIES}
+    missing = mism = 0
+    n_checked = 0
+    for k in SPECIES:
+        o = orc["final"][k]
+        for j, pid in enumerate(o["id"].tolist()):
+            i = gi[k].get(int(pid))
+            if i is None:
+                missing += 1
+                continue
+            n_checked += 1
+            pm = np.sqrt(o["px"][j] ** 2 + o["py"][j] ** 2 + o["pz"][j] ** 2)
+            dp = max(abs(g[k][c][i] - o[c][j]) for c in ("px", "py", "pz"))
+            to, tg = o["tau"][j], g[k]["tau"][i]
+            same_tau = (np.isinf(to) and np.isinf(tg)) or abs(tg - to) <= 1e-9 * max(abs(to), 1.0)
+            if dp > 1e-10 * max(pm, 1.0) or not same_tau or g[k]["weight"][i] != o["weight"][j]:
+                mism += 1
+    # a history can differ only through a decision within the FP64 rounding bound of zero (expected: none)
+    assert n_checked > 2 * SUB and missing + mism <= 3, (missing, mism, n_checked)
+
+    # 2. FP32 against FP64, history by history (ids) and in counts
+    f32, f64 = r32["final"], r64["final"]
+    i32 = {k: _by_id(f32[k]) for k in SPECIES}
+    differ = 0
+    for k in ("electrons", "photons"):
+        d64, d32 = f64[k], f32[k]
+        prim = np.nonzero(_is_primary(d64["id"]))[0]
+        j32 = np.array([i32[k][int(p)] for p in d64["id"][prim]])
+        p64 = np.stack([d64[c][prim] for c in ("px", "py", "pz")], 1)
+        p32 = np.stack([d32[c][j32].astype(np.float64) for c in ("px", "py", "pz")], 1)
+        scale = np.maximum(np.linalg.norm(p64, axis=1), 1.0)
+        differ += int(np.sum(np.max(np.abs(p32 - p64), axis=1) > 1e-5 * scale))
+    frac = differ / (2 * N)
+    print(f"FP32 vs FP64 over {STEPS} steps: primaries with a different history: {differ} ({frac:.2e})")
+    assert frac < 5e-3
+    for key in ("qs_events", "bw_events", "photons_kept", "pairs"):
+        a, b = r32["stats"][key], r64["stats"][key]
+        print(f"  {key}: FP32 {a}  FP64 {b}  rel diff {(a - b) / b:+.2e}")
+        assert abs(a - b) <= 2e-3 * b + 10, key
+    cs32 = np.cumsum(r32["per_step"][:, [0, 1]], axis=0)
+    cs64 = np.cumsum(r64["per_step"][:, [0, 1]], axis=0)
+    assert np.all(np.abs(cs32 - cs64) <= 2e-3 * cs64 + 10)
+    for key in ("qs", "bw"):
+        h32 = np.histogram(r32["fire_chi"][key], CHI_EDGES)[0]
+        h64 = np.histogram(r64["fire_chi"][key], CHI_EDGES)[0]
+        assert np.all(np.abs(h32 - h64) <= 5e-3 * h64 + 10), (key, h32, h64)
+    s32, s64 = _secondary_spectra(f32), _secondary_spectra(f64)
+    for a, b in zip(s32, s64):
+        assert np.all(np.abs(a - b) <= 1e-2 * b + 10), (a, b)
+
+    # 3. both against the oracle's subsample, statistically
+    for r in (r64, r32):
+        ps_g = {"qs": int(r["counts"][:, 0].sum() + r["counts"][:, 1].sum()), "bw": int(r["counts"][:, 2].sum())}
+        for key in ("qs", "bw"):
+            hg = np.histogram(r["fire_chi"][key], CHI_EDGES)[0]
+            ho = np.histogram(orc["fire_chi"][key], CHI_EDGES)[0]
+            assert np.all(_poisson_close(hg, ps_g[key], ho, orc["ps"][key])), (key, hg, ho)
+        sg, so = _secondary_spectra(r["final"]), _secondary_spectra(orc["final"])
+        for a, b in zip(sg, so):
+            assert np.all(_poisson_close(a, 2 * N, b, 2 * SUB)), (a, b)
+    assert orc["n_qs"] > 1000 and orc["n_bw"] > 100
+
+    # 4. energy: the sum over the three species, every step
+    for r, tol in ((r64, 1e-12), (r32, 1e-7)):
+        e = r["energy"][:, 0]
+        drift = np.max(np.abs(e / e[0] - 1.0))
+        print(f"  energy drift over {STEPS} steps: {drift:.2e}")
+        assert drift <= tol

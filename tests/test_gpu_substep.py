@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import FIELDS, as_f64, check_substep_fp32, gpu_tables, sort_by_id, tau_bound, tau_eff
+from helpers import (FIELDS, as_f64, check_substep_fp32, compare_states as _compare, gpu_tables,
+                     margin_ids as _margin_ids, sort_by_id, tau_bound, tau_eff)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,46 +52,6 @@ def _run_gpu(api, t, host, prec, dt, seed, step, extra=3.0, threshold=0.0, caps=
                     photon_threshold=threshold, stats=stats, qs_chi_cut=cuts[0], bw_chi_cut=cuts[1])
     torch.cuda.synchronize()
     return {k: bufs[k].to_host() for k in SPECIES}, stats.as_dict(), fire
-
-
-def _margin_ids(ot, host64, dt, tol, seed, step, cuts=(0.0, 0.0)):
-    """ids of particles whose decision lies within the error bound (of the
-    firing test or of a chi cut-off), and their children."""
-    out = set()
-    for k, proc in (("electrons", 0), ("positrons", 0), ("photons", 1)):
-        tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt, cuts[proc])
-        b = tau_bound(ot, proc, host64[k], chi, rate, dt, tol)
-        near_cut = np.abs(chi - cuts[proc]) <= 1e-9 * cuts[proc]
-        for pid in host64[k]["id"][(np.abs(tn) <= b) | near_cut].tolist():
-            out.add(pid)
-            out |= set(oracle.child_ids(seed, pid, step))
-    return out
-
-
-def _compare(got, ref, prec_f32, tol, exclude=frozenset()):
-    worst = {}
-    for k in SPECIES:
-        g, r = sort_by_id(got[k]), sort_by_id({kk: ref[k][kk] for kk in got[k]})
-        if exclude:
-            keep_g = ~np.isin(g["id"], list(exclude))
-            keep_r = ~np.isin(r["id"], list(exclude))
-            g = {kk: v[keep_g] for kk, v in g.items()}
-            r = {kk: v[keep_r] for kk, v in r.items()}
-        assert np.array_equal(g["id"], r["id"]), f"{k}: id sets differ ({len(g['id'])} vs {len(r['id'])})"
-        gt = tau_eff(g, prec_f32)
-        fin = np.isfinite(r["tau"])
-        assert np.array_equal(np.isfinite(gt), fin), f"{k}: removed-particle mask"
-        pm = np.sqrt(r["px"] ** 2 + r["py"] ** 2 + r["pz"] ** 2)
-        e = 0.0
-        for c in ("px", "py", "pz"):
-            e = max(e, float(np.max(np.abs(g[c] - r[c]) / np.maximum(pm, 1e-300), initial=0)))
-        et = float(np.max(np.abs(gt[fin] - r["tau"][fin]) / np.maximum(np.abs(r["tau"][fin]), 1.0), initial=0))
-        for c in ("ex", "ey", "ez", "bx", "by", "bz", "weight"):
-            assert np.array_equal(g[c].astype(np.float64), r[c]), f"{k}: {c} copied exactly"
-        worst[k] = (e, et)
-        assert e <= tol, f"{k}: momentum rel err {e:.3e}"
-        assert et <= tol, f"{k}: tau err {et:.3e}"
-    return worst
 
 
 def test_substep_fp64_parity(api, tabs):
