@@ -39,6 +39,14 @@ BYTES_F64 = 88  # p, E, B, tau read (80) + tau written (8)
 FALLBACK_HBM_GBS = 6800.0
 
 
+def headline_config(n: int, ws: int) -> dict:
+    """The headline workload's description (the same in both arms)."""
+    return {"workload": WORKLOAD, "particles": 2 * n, "electrons": n, "photons": n, "dt": DT,
+            "tables": "256 / 256x256, FP64 generated, FP32 copies", "seed": SEED,
+            "l2": "inputs (%.1f GB) larger than L2, no flush" % (2 * n * 48 / 1e9),
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -108,10 +116,6 @@ def profile_record(name: str, key: str):
 def traffic_record():
     """DRAM bytes per particle of the FP32 evolution kernel (the bulk-copy pipeline)."""
     return profile_record("evolve_bulk_kernel_fp32_traffic.txt", "dram_bytes_per_particle")
-
-
-# FP64 pipe of GB300: 2 thread instructions per SM per clock (profiles/evolve_kernel_fp64_pipe.md)
-FP64_INST_PER_SM_CLOCK = 2.0
 
 
 class Clocks:
@@ -262,29 +266,32 @@ def time_substep(api, t, bufs, fire, steps, warmup, ws, step0=0, evolve_events=T
 
 
 def mlp_leg(api, tabs, bufs, fire, args, ws):
-    """The substep with the learned sampler in place of the 2-D tables, and the
-    two samplers alone on 1e8 (chi, U) pairs."""
+    """The learned sampler: both networks trained on 1e7 exact samples each (the
+    GPU's exact inverse CDF, no table) by the library's kernels; the substep
+    with the network in place of the 2-D tables; the two samplers alone on 1e8
+    (chi, U) pairs; their KS distance to the exact inverse CDF in 5 chi bins;
+    and the hard-photon tail P(xi > 0.99) at chi = 9."""
     import math
 
+    import numpy as np
     import torch
 
     from paper_2110_00256_gb300 import surrogate
-    fine = api.qed_tables_generate(api.table_params(qs_n_chi=512, qs_n_xi=1024, bw_n_chi=512, bw_n_xi=1024))
-    mlp = api.Mlp(fine, seed=3)
+    mlp = api.Mlp(tabs, seed=3)
     t0 = time.perf_counter()
-    train = {p: surrogate.train(mlp, fine, p, n_samples=4_000_000, epochs=8, batch=65536) for p in (0, 1)}
+    train = {p: surrogate.train(mlp, tabs, p, n_samples=10_000_000, epochs=3) for p in (0, 1)}
     train_s = time.perf_counter() - t0
     k = max(3, args.steps // 4)
     r = time_substep(api, tabs, bufs, fire, k, 2, ws, step0=1000, mlp=mlp)
     ms = max_over_ranks(ws, r["ms"])
     out = {"value": sum_over_ranks(ws, r["n_before"] * k) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k,
-           "train_s": round(train_s, 2), "train_final_loss": {p: round(train[p]["final_loss"], 6) for p in train}}
+           "train_s": round(train_s, 2), "train_samples_per_process": 10_000_000, "train_epochs": 3,
+           "train_final_loss": {p: round(train[p]["final_loss"], 6) for p in train}}
     n = 100_000_000
     g = torch.Generator(device="cuda")
     g.manual_seed(11)
     for p, name in ((0, "qs"), (1, "bw")):
-        ax = tabs.params.qs if p == 0 else tabs.params.bw
-        lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
+        lo, hi = (math.log(v) for v in surrogate.chi_range(tabs, p))
         chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
         u = torch.rand(n, generator=g, device="cuda", dtype=torch.float64).clamp_(1e-15, 1 - 1e-15)
         o = torch.empty_like(chi)
@@ -300,13 +307,29 @@ def mlp_leg(api, tabs, bufs, fire, args, ws):
             torch.cuda.synchronize()
             out[f"{name}_{label}_samples_per_s"] = 3 * n / (e0.elapsed_time(e1) * 1e-3)
         del chi, u, o
-        ks = surrogate.compare(mlp, fine, p, n=2_000_000, prec=api.QED_F64)
-        out[f"{name}_ks_table256_f32_vs_fp64_table"] = round(
-            surrogate.compare_tables(tabs, api.QED_F32, fine, api.QED_F64, p, n=2_000_000), 6)
-        out[f"{name}_ks_mlp_vs_fp64_table"] = round(ks["overall"], 5)
-        out[f"{name}_ks_mlp_vs_fp64_table_worst_bin"] = round(max(ks["bins"]), 5)
-    out["params_bytes_bf16"] = 2 * 4417
-    out["table_bytes_fp32_256x256"] = 2 * 256 * 256 * 4
+        torch.cuda.empty_cache()
+        kn = surrogate.compare(lambda c, uu: mlp.sample(p, c, uu), tabs, p, n=2_000_000)
+        kt = surrogate.compare(lambda c, uu: api.qed_table_sample(tabs, p, api.QED_F32, c, uu), tabs, p,
+                               n=2_000_000)
+        out[f"{name}_ks_vs_exact"] = {"mlp_overall": round(kn["overall"], 5),
+                                      "mlp_bins": [round(v, 5) for v in kn["bins"]],
+                                      "table256_f32_overall": round(kt["overall"], 5),
+                                      "table256_f32_bins": [round(v, 5) for v in kt["bins"]]}
+    # P(xi > 0.99 | chi = 9): the smallest U mapped above 0.99, on a grid dense near U = 1
+    uu = np.concatenate([np.linspace(0.5, 1 - 1e-3, 20000), 1 - np.logspace(-3, -12, 20000)])
+    ut = torch.tensor(uu, dtype=torch.float64, device="cuda")
+    ct = torch.full_like(ut, 9.0)
+
+    def tail(x):
+        above = np.nonzero(x.cpu().numpy() > 0.99)[0]
+        return float(1.0 - uu[above[0]]) if len(above) else 0.0
+
+    out["qs_tail_chi9_xi_gt_0.99"] = {"exact": tail(api.qed_exact_sample(0, torch.tensor([9.0], dtype=torch.float64,
+                                                                                          device="cuda"), ut)),
+                                      "mlp": tail(mlp.sample(0, ct, ut)),
+                                      "table256_f32": tail(api.qed_table_sample(tabs, 0, api.QED_F32, ct, ut))}
+    out["params_bytes_bf16_per_network"] = 2 * 4417
+    out["table_bytes_fp32_256x256_per_process"] = 2 * 256 * 256 * 4
     return out
 
 
@@ -477,6 +500,35 @@ def batched_leg(api, tabs, ws, steps=10, warmup=3):
     return out
 
 
+def subsample_step(api, tabs, bufs, fire, step, m=500_000):
+    """One substep of the headline state with every (n/m)-th electron and photon
+    copied to the host before and after, and the firing lists mapped to them."""
+    import numpy as np
+    import torch
+    out = {"pre": {}, "post": {}, "fire": {}, "step": step, "n_particles": 0}
+    sel = {}
+    for k in ("electrons", "photons"):
+        n = int(bufs[k].count.item())
+        stride = max(1, n // m)
+        idx = torch.arange(0, stride * min(m, n), stride, device="cuda")
+        sel[k] = (idx, stride)
+        out["n_particles"] += n
+        out["pre"][k] = {c: bufs[k].arrays[c].index_select(0, idx).cpu().numpy()
+                         for c in ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz", "tau", "tau_c")}
+        out["pre"][k]["id"] = bufs[k].arrays["id"].index_select(0, idx).cpu().numpy().view(np.uint64)
+    api.SubstepCall(tabs, bufs["electrons"], bufs["positrons"], bufs["photons"], fire, DT, SEED)(step)
+    torch.cuda.synchronize()
+    for k, j in (("electrons", 0), ("photons", 2)):
+        idx, stride = sel[k]
+        out["post"][k] = {c: bufs[k].arrays[c].index_select(0, idx).cpu().numpy() for c in ("tau", "tau_c")}
+        nf = int(fire[j].count.item())
+        fi = fire[j].idx[:nf].cpu().numpy()
+        fc = fire[j].chi[:nf].cpu().numpy()
+        keep = (fi % stride == 0) & (fi // stride < idx.numel())
+        out["fire"][k] = ((fi[keep] // stride).astype(np.int64), fc[keep])
+    return out
+
+
 def chi_for_inputs(d, photon):
     """chi of the unscaled synthetic particles (§2 definition, FP64 numpy), only
     to rescale their fields so that chi follows the workload's distribution."""
@@ -588,29 +640,106 @@ def schwinger_leg(api, ws):
     return out
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+_ORACLE_TIMING = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2110_00256_gb300 import workloads
+ot = oracle.tables()
+m = {m}
+sp = {{"electrons": workloads.paper_benchmark(m, 11, 0), "photons": workloads.paper_benchmark(m, 12, 10 ** 12),
+      "positrons": workloads.paper_benchmark(0, 13, 2 * 10 ** 12)}}
+steps, t0 = 0, time.perf_counter()
+while True:
+    out = oracle.substep(ot, sp, dt={dt}, seed={seed}, step=steps)
+    sp = {{k: {{c: out[k][c] for c in sp[k]}} for k in sp}}
+    steps += 1
+    if time.perf_counter() - t0 > {seconds}:
+        break
+print(json.dumps({{"steps": steps, "seconds": time.perf_counter() - t0}}))
+"""
+
+
+def _time_oracle(m: int, seconds: float, threads: int) -> dict:
+    """The oracle's substep on 2m particles of the §4 distribution, in a child
+    process with `threads` OpenMP threads, for about `seconds`."""
+    code = _ORACLE_TIMING.format(root=ROOT, m=m, dt=DT, seed=SEED, seconds=seconds)
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 2 * m * d["steps"] / d["seconds"], "steps": d["steps"], "seconds": round(d["seconds"], 1)}
+
+
+def cpu_baseline(seconds=12.0, check=None):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    all cores and one core, each in its own process; and, when `check` holds a
+    GPU substep of a subsample of the headline workload, its error statement."""
+    cores = os.cpu_count() or 1
+    m = 250_000
+    allc = _time_oracle(m, seconds, cores)
+    one = _time_oracle(20_000, seconds / 2, 1)
+    out = {"value": allc["value"], "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+           "sample": f"{2 * m} particles (paper §4 distribution, 256/256x256 FP64 oracle tables), {allc['steps']} "
+                     f"substeps, {allc['seconds']} s wall; evolution OpenMP-parallel over particles, events serial",
+           "one_core": {"value": one["value"], "unit": UNIT, "cores": 1,
+                        "sample": f"40000 particles, {one['steps']} substeps, {one['seconds']} s wall"}}
+    if check is not None:
+        out["error_vs_oracle"] = error_vs_oracle(**check)
+    return out
+
+
+def error_vs_oracle(pre: dict, post: dict, fire: dict, step: int, n_particles: int) -> dict:
+    """The FP32 substep's error against the FP64 oracle on a subsample of the
+    headline workload (the oracle started from the GPU's pre-step state):
+    optical depths of the particles that did not fire against the rounding bound
+    of the FP32 evaluation, chi of the firing ones, and the firing decisions
+    that differ with their margin m = |tau_new| / tau_old."""
     import numpy as np
 
     import oracle
-    from paper_2110_00256_gb300 import workloads
     ot = oracle.tables()
-    m = 250_000
-    sp = {"electrons": workloads.paper_benchmark(m, 11, 0), "photons": workloads.paper_benchmark(m, 12, 10 ** 12),
-          "positrons": workloads.paper_benchmark(0, 13, 2 * 10 ** 12)}
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        out = oracle.substep(ot, sp, dt=DT, seed=SEED, step=steps)
-        sp = {k: {c: out[k][c] for c in sp[k]} for k in sp}
-        steps += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 2 * m * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
-            "sample": f"{2 * m} particles (paper §4 distribution, 256/256x256 FP64 oracle tables), {steps} substeps, "
-                      f"{el:.1f} s wall; evolution OpenMP-parallel over particles, events serial"}
+    res = {"particles": 0, "max_tau_err_over_bound": 0.0, "max_rel_tau_err": 0.0, "max_rel_chi_err_firing": 0.0,
+           "events_checked": 0, "decisions_differing": 0, "max_margin_of_differing": 0.0}
+    for name, proc in (("electrons", 0), ("photons", 1)):
+        h = pre[name]
+        n = len(h["id"])
+        res["particles"] += n
+        tau_old = h["tau"].astype(np.float64) - h["tau_c"].astype(np.float64)
+        inp = {c: h[c].astype(np.float64) for c in ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")}
+        inp["tau"] = tau_old
+        tn, chi, rate, f = oracle.evolve(proc, ot, inp, DT)
+        p2 = inp["px"] ** 2 + inp["py"] ** 2 + inp["pz"] ** 2
+        en = np.sqrt(p2) if proc else np.sqrt(1.0 + p2)
+        S = en * np.sqrt(inp["ex"] ** 2 + inp["ey"] ** 2 + inp["ez"] ** 2) + \
+            np.sqrt(p2) * np.sqrt(inp["bx"] ** 2 + inp["by"] ** 2 + inp["bz"] ** 2)
+        dchi = 1e-5 * S + 16 * 2.0 ** -53 * S * S / np.maximum(chi, 1e-300)
+        r_hi = ot.rates(proc, chi + dchi, en)
+        r_lo = ot.rates(proc, np.maximum(chi - dchi, 0.0), en)
+        bound = 1e-5 * np.abs(tau_old) + DT * (np.maximum(np.abs(r_hi - rate), np.abs(r_lo - rate)) + 1e-5 * rate)
+        gf = np.zeros(n, dtype=bool)
+        gf[fire[name][0]] = True
+        quiet = ~gf & ~f
+        t_gpu = post[name]["tau"].astype(np.float64) - post[name]["tau_c"].astype(np.float64)
+        err = np.abs(t_gpu[quiet] - tn[quiet])
+        res["max_tau_err_over_bound"] = max(res["max_tau_err_over_bound"],
+                                            float(np.max(err / (bound[quiet] + 1e-300), initial=0.0)))
+        res["max_rel_tau_err"] = max(res["max_rel_tau_err"],
+                                     float(np.max(err / np.maximum(np.abs(tn[quiet]), 1e-30), initial=0.0)))
+        both = gf & f
+        idx, chig = fire[name]
+        sel = both[idx]
+        if sel.any():
+            res["max_rel_chi_err_firing"] = max(res["max_rel_chi_err_firing"],
+                                                float(np.max(np.abs(chig[sel] - chi[idx[sel]]) / chi[idx[sel]])))
+        res["events_checked"] += int(both.sum())
+        diff = np.nonzero(gf != f)[0]
+        res["decisions_differing"] += int(len(diff))
+        if len(diff):
+            res["max_margin_of_differing"] = max(res["max_margin_of_differing"],
+                                                 float(np.max(np.abs(tn[diff]) / np.abs(tau_old[diff]))))
+    res["sample"] = (f"{res['particles']} particles (every {n_particles // max(res['particles'], 1)}-th of the "
+                     f"headline's 1e8) through one FP32 substep, step {step}")
+    return res
 
 
 def cpu_model() -> str:
@@ -670,11 +799,7 @@ def gpu_main(args):
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": {"workload": WORKLOAD, "particles": 2 * n, "electrons": n, "photons": n, "dt": DT,
-                         "tables": "256 / 256x256, FP64 generated on the GPU, FP32 copies", "seed": SEED,
-                         "l2": "inputs (%.1f GB) larger than L2, no flush" % (2 * n * 48 / 1e9),
-                         "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                         "table_generation_ms": round(gen_ms, 1)},
+              "config": headline_config(n, ws), "table_generation_ms": round(gen_ms, 1),
               "roofline": roofline,
               "gpu_launches": 4 * args.steps,  # zero3, evolution, the three event lists, clamp_all
               "events_per_step": {k: v / (args.warmup + args.steps) for k, v in r["stats"].items() if v}}
@@ -693,6 +818,13 @@ def gpu_main(args):
         variants[name] = {"evolve_ms": round(evm, 4), "hbm_gbs": round(BYTES_F32 * rv["n_before"] / (evm * 1e-3) / 1e9, 1),
                           "wait_timeout": rv["stats"].get("wait_timeout", 0)}
     result["evolve_variants"] = variants
+
+    # one more substep of the same state, kept for the error statement against
+    # the oracle (cpu_baseline leg): a subsample of 1e6 particles, every n/5e5-th
+    # electron and photon, before and after the step, with the firing lists
+    check = None
+    if rank == 0 and not args.no_cpu_baseline:
+        check = subsample_step(api, tabs, bufs, fire, 2000)
 
     if not args.no_e2e:
         k = max(4, min(args.steps, 8))
@@ -716,16 +848,21 @@ def gpu_main(args):
                                           "ms_per_step": ms64 / max(3, args.steps // 4),
                                           "evolve_ms": round(ev64, 4), "hbm_gbs": round(ach64, 1),
                                           "hbm_frac": round(ach64 / hbm, 4)}}
+        # the FP64 pipe's peak, measured by a kernel of nothing but FMA chains
+        probe = api.qed_probe_fp64_fma()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = clk["sm_mhz"] if clk else 2070.0
+        result["paths"]["fp64_table"]["fp64_fma_probe"] = {
+            "fma_per_s": probe["fma_per_s"], "per_sm_per_clock": round(probe["fma_per_s"] / (sms * mhz * 1e6), 3),
+            "clock_mhz_assumed": mhz, "ms": round(probe["ms"], 3)}
         ipp = profile_record("evolve_kernel_fp64_insts.txt", "fp64_inst_per_particle")
         if ipp:
-            import torch as _t
-            peak64 = FP64_INST_PER_SM_CLOCK * _t.cuda.get_device_properties(0).multi_processor_count * \
-                (clk["sm_mhz"] if clk else 2070.0) * 1e6
+            peak64 = probe["fma_per_s"]
             ach_i = ipp * r64["n_before"] / (ev64 * 1e-3)
             result["paths"]["fp64_table"]["roofline"] = {
                 "bound": "alu", "kernel": "evolve_kernel<double,2,4,3>", "unit": "FP64 instructions/s",
                 "achieved": ach_i, "peak": peak64, "frac": round(ach_i / peak64, 4),
-                "peak_kind": "2 FP64 instructions per SM per clock x SMs x the sampled SM clock",
+                "peak_kind": "measured: qed_probe_fp64_fma (dependent DFMA chains) on this GPU",
                 "fp64_inst_per_particle": ipp}
         bufs, fire = b64, f64
         del b64, f64
@@ -765,7 +902,7 @@ def gpu_main(args):
         result.setdefault("paths", {})["full_qs_bw_1000_steps"] = longrun_leg(api, tabs, ws, rank)
 
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline()
+        result["cpu_baseline"] = cpu_baseline(check=check)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if ws > 1:
@@ -804,7 +941,7 @@ def reference_main(args):
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+                      "data": "synthetic", "config": headline_config(args.n, ws),
                       "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                        "cpu": cpu_model(), "sample": sample},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),

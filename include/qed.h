@@ -510,6 +510,34 @@ qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const double *d_ch
 qed_status qed_table_sample(const qed_tables *t, qed_process proc, qed_precision prec, const double *d_chi,
                             const double *d_u, int64_t n, double *d_xi, void *stream);
 
+/* The exact inverse CDF, without tables (the learned sampler's training
+ * targets, and a reference for both samplers): for each of m values chi[i]
+ * (device FP64) and each of k draws u[i k + j] (device FP64 in [0, 1]),
+ * xi[i k + j] solves P(chi_i, xi) = u to ~1e-13 relative: QS (§3.2, the
+ * number spectrum S(chi, xi)/xi of Eq. (qs_diff_cross)) gives chi_gamma/chi;
+ * BW (§3.1, Eq. (bw_prob_dist)) the electron's chi_-/chi_g, u <= 1/2 sampling
+ * the electron as in the table path.  FP64 quadrature on the GPU: per chi the
+ * cumulative integral over a fine grid of 1024 intervals (Gauss-Legendre; the
+ * QS grid is uniform in ln(xi / (1 - xi)), the BW grid in ln xi), per draw the
+ * bracketing interval, a cubic Hermite first guess and Newton steps on the
+ * partial integral.  d_work: device FP64 scratch of at least QED_EXACT_WORK(m)
+ * entries.  Stream-ordered; m <= 2^31. */
+#define QED_EXACT_WORK(m) ((int64_t)(m) * 2051)
+qed_status qed_exact_sample(qed_process proc, const double *d_chi, int64_t m, const double *d_u, int64_t k,
+                            double *d_xi, double *d_work, int64_t work_capacity, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* measurement                                                                */
+/* ------------------------------------------------------------------------- */
+/* Not part of the method: the FP64 throughput of this GPU, measured by a kernel
+ * of nothing but dependent fused multiply-add chains (8 per thread, 256 threads
+ * per CTA, ctas_per_sm CTAs per SM, `iters` FMAs per chain), timed with CUDA
+ * events around one launch after a warm-up launch.  *fma_per_s receives FMA
+ * instructions per second (each thread's FMA counted once); d_sink: one device
+ * double (never written in practice).  Synchronises `stream`. */
+qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
+                              float *ms_out, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* the substep without caller-provided working memory                        */
 /* ------------------------------------------------------------------------- */

@@ -12,11 +12,15 @@ defines it:
   layer 1    h1 = gelu(W1 x + b1)              (64)
   layer 2    h2 = gelu(W2 bf16(h1) + b2)       (64), bf16 = round to bfloat16
   layer 3    y  = W3 . h2 + b3
-  output     QS: ln xi = min(y + 3 ln U, 0)    BW: xi_s = clamp(y, 0, 1/2)
-             (xi_s is the electron's fraction if U <= 1/2, else the positron's)
+  output     QS: ln(xi / (1 - xi)) = y + 3 ln U + L(chi_c),  L(chi) = ln(chi / (1 + chi))
+             BW: xi_s = clamp(1/2 - w(chi_c) y, 0, 1/2),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
+             (xi_s is the electron's fraction if U <= 1/2, else the positron's;
+             L and w centre and scale y: xi ~ U^3 as U -> 0 and grows with chi,
+             the logit resolves 1 - xi at the hard end, and the pair split
+             narrows around 1/2 with width ~ sqrt(3 chi / 64))
   gelu(x)    = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))   (Hendrycks & Gimpel)
-  loss       mean over the batch of (y - t)^2, with t = ln xi* - 3 ln U (QS) or
-             t = xi_s* (BW), xi* the FP64 table sample of the same (chi, U)
+  loss       mean over the batch of (y - t)^2, with t the y whose output is xi*,
+             xi* the reference sample of the same (chi, U)
 
 Weights are used as bfloat16 (a master copy is kept in FP32 for Adam); the
 rounding of h1 is treated as the identity in the backward pass.
@@ -90,12 +94,23 @@ def forward(theta, X, round_bf16=True):
     return y, (X, z1, h1q, z2, h2, W1, W2, W3)
 
 
-def targets(proc: int, u, xi):
+def centre_scale(proc: int, chi, chi_min, chi_max):
+    """L(chi_c) for QS, w(chi_c) for BW (the output map above)."""
+    c = np.clip(np.asarray(chi, dtype=np.float64), chi_min, chi_max)
+    if proc == 0:
+        return np.log(c) - np.log1p(c)
+    return 0.5 * np.sqrt(c / (c + 16.0 / 3.0))
+
+
+def targets(proc: int, chi, u, xi, chi_min, chi_max):
+    """t with output(t) = xi; for BW, xi is the electron's fraction."""
     u = np.asarray(u, dtype=np.float64)
     xi = np.asarray(xi, dtype=np.float64)
+    cs = centre_scale(proc, chi, chi_min, chi_max)
     if proc == 0:
-        return np.log(xi) - 3.0 * np.log(u)
-    return xi  # folded fraction of the sampled lepton, in [0, 1/2]
+        return np.log(xi) - np.log1p(-xi) - 3.0 * np.log(u) - cs
+    xs = np.where(u <= 0.5, xi, 1.0 - xi)  # folded fraction of the sampled lepton, in [0, 1/2]
+    return (0.5 - xs) / cs
 
 
 def loss_and_grad(theta, X, t, round_bf16=True):
@@ -117,12 +132,14 @@ def loss_and_grad(theta, X, t, round_bf16=True):
     return loss, g
 
 
-def output(proc: int, y, u):
-    """Sampled xi from the network output (the output map above)."""
+def output(proc: int, y, chi, u, chi_min, chi_max):
+    """Sampled xi from the network output (the output map above): QS chi_gamma/chi,
+    BW the folded fraction xi_s of the lepton that U selects."""
     u = np.asarray(u, dtype=np.float64)
+    cs = centre_scale(proc, chi, chi_min, chi_max)
     if proc == 0:
-        return np.exp(np.minimum(y + 3.0 * np.log(u), 0.0))
-    return np.clip(y, 0.0, 0.5)
+        return 1.0 / (1.0 + np.exp(-(y + 3.0 * np.log(u) + cs)))
+    return np.clip(0.5 - cs * np.asarray(y, dtype=np.float64), 0.0, 0.5)
 
 
 def adam(theta, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):

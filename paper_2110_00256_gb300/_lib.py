@@ -27,6 +27,10 @@ QED_MAX_TABLE_N = 1024
 QED_EW_WAIT_TIMEOUT, QED_EW_NONFINITE, QED_EW_CAPACITY, QED_EW_FIRE_OVERFLOW = 1, 2, 4, 8
 
 
+def QED_EXACT_WORK(m: int) -> int:
+    return int(m) * 2051
+
+
 def QED_COMPACT_WORK(cap: int) -> int:
     return 2 * int(cap) + (int(cap) + 2047) // 2048 + 8
 
@@ -135,6 +139,8 @@ SIGNATURES = {
     "qed_device_status": (_S, [_P, C.POINTER(C.c_uint32), C.c_int32]),
     "qed_species_energy": (_S, [C.POINTER(Species), _S, C.c_int32, _P, _P]),
     "qed_compact_species": (_S, [C.POINTER(Species), _S, _P, _I64, _P, _P]),
+    "qed_exact_sample": (_S, [_S, _P, _I64, _P, _I64, _P, _P, _I64, _P]),
+    "qed_probe_fp64_fma": (_S, [_I64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_float), _P]),
 }
 QED_MLP_PARAMS = 4417
 QED_MAX_PATCHES = 1024

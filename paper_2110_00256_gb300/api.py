@@ -25,7 +25,7 @@ __all__ = [
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
     "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields", "qed_push_substep_batched",
     "qed_schwinger_pairs",
-    "qed_push_batched", "qed_device_status", "qed_species_energy", "qed_compact_species", "CompactWork",
+    "qed_push_batched", "qed_exact_sample", "qed_probe_fp64_fma", "qed_device_status", "qed_species_energy", "qed_compact_species", "CompactWork",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -497,3 +497,28 @@ def qed_compact_species(sp: SpeciesBuffers, work: CompactWork, stats: Stats | No
     s = sp.struct()
     check(lib().qed_compact_species(C.byref(s), sp.prec, work.t.data_ptr(), int(work.t.numel()),
                                     stats.t.data_ptr() if stats is not None else None, _stream(stream)))
+
+
+def qed_exact_sample(proc: int, chi_rows: torch.Tensor, u: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """The exact inverse CDF (include/qed.h) for m chi values and k draws each:
+    u and the result have shape (m, k), FP64 on the device."""
+    m = int(chi_rows.numel())
+    k = int(u.numel()) // max(m, 1)
+    if u.numel() != m * k:
+        raise ValueError("u must hold k draws for each of the m chi values")
+    if out is None:
+        out = torch.empty_like(u)
+    work = torch.empty(_lib.QED_EXACT_WORK(m), dtype=torch.float64, device=chi_rows.device)
+    check(lib().qed_exact_sample(int(proc), chi_rows.data_ptr(), m, u.data_ptr(), k, out.data_ptr(), work.data_ptr(),
+                                 int(work.numel()), _stream(stream)))
+    return out
+
+
+def qed_probe_fp64_fma(iters: int = 200_000, ctas_per_sm: int = 4, stream=None) -> dict:
+    """FP64 FMA instructions per second of this GPU (include/qed.h)."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    r, ms = C.c_double(), C.c_float()
+    check(lib().qed_probe_fp64_fma(int(iters), int(ctas_per_sm), sink.data_ptr(), C.byref(r), C.byref(ms),
+                                   _stream(stream)))
+    return {"fma_per_s": r.value, "ms": ms.value}

@@ -227,6 +227,12 @@ __device__ __forceinline__ const float *seg_stream(const EvolveSeg<float> &g, in
 
 __device__ __forceinline__ bool seg_wait(uint64_t *bar, uint32_t parity, volatile int *abort, long long limit)
 {
+    if (limit < kWaitCycles) {  // a caller's shorter limit: non-blocking probes (see evolve.cu)
+        const long long t0 = clock64();
+        while (!mbar_peek(bar, parity))
+            if (*abort || clock64() - t0 > limit) return false;
+        return true;
+    }
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {

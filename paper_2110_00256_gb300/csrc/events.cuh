@@ -122,11 +122,10 @@ __device__ __forceinline__ void qs_event_chunk(const EventSeg<T> &g, const Event
     const double u = uniform53(w.x, w.y);
     T xi;
     if constexpr (MLP) {
-        float x1, x2;
-        mlp_features(c.mlpv, (double)chi, u, x1, x2);
+        const MlpIn in = mlp_input(c.mlpv, (double)chi, u);
         const int wib = threadIdx.x >> 5;
-        const float y = mlp_forward_warp(S.net, S.h1[wib], S.y[wib], x1, x2);
-        xi = valid ? (T)mlp_output(QED_PROC_QS, y, u) : T(0);
+        const float y = mlp_forward_warp(S.net, S.h1[wib], S.y[wib], in.x1, in.x2);
+        xi = valid ? (T)mlp_output(QED_PROC_QS, y, in) : T(0);
     } else {
         xi = valid ? qs_sample_xi<T>(c.tab, chi, sample_uniform<T>(u)) : T(0);
     }
@@ -183,11 +182,10 @@ __device__ __forceinline__ void bw_event_chunk(const EventSeg<T> &g, const Event
     const double u = uniform53(w.x, w.y);
     T xm, xp;  // electron and positron fractions of the photon's chi
     if constexpr (MLP) {
-        float x1, x2;
-        mlp_features(c.mlpv, (double)chi, u, x1, x2);
+        const MlpIn in = mlp_input(c.mlpv, (double)chi, u);
         const int wib = threadIdx.x >> 5;
-        const float y = mlp_forward_warp(S.net, S.h1[wib], S.y[wib], x1, x2);
-        const double em = mlp_output(QED_PROC_BW, y, u);
+        const float y = mlp_forward_warp(S.net, S.h1[wib], S.y[wib], in.x1, in.x2);
+        const double em = mlp_output(QED_PROC_BW, y, in);
         xm = valid ? (T)em : T(0);
         xp = valid ? (T)(1.0 - em) : T(0);
     } else {

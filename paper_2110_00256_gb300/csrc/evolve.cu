@@ -117,6 +117,14 @@ constexpr int kBulkArrays = 11;
 // bounded wait (limit cycles) that also gives up as soon as another warp has given up
 __device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity, volatile int *abort, long long limit)
 {
+    if (limit < kWaitCycles) {
+        // a caller's shorter limit: probe without the hardware's suspended wait,
+        // which by itself can outlast a limit of a few cycles
+        const long long t0 = clock64();
+        while (!mbar_peek(bar, parity))
+            if (*abort || clock64() - t0 > limit) return false;
+        return true;
+    }
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {

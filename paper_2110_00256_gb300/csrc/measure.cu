@@ -1,0 +1,53 @@
+// measure.cu -- a standalone FP64 throughput probe: the peak against which the
+// FP64 evolution kernel (bound by GB300's FP64 pipe) is judged, measured by a
+// kernel that does nothing but dependent chains of fused multiply-adds.
+#include "launch.cuh"
+
+namespace qed {
+
+constexpr int kProbeChains = 8;  // independent chains per thread (hide the FMA latency)
+
+__global__ void __launch_bounds__(256) fp64_fma_kernel(int64_t iters, double a, double b, double *sink)
+{
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c];
+    if (s == 1234.5678) sink[0] = s;  // keeps the chains alive; never true for these inputs
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
+                                         float *ms_out, void *stream)
+{
+    clear_error();
+    if (iters <= 0 || ctas_per_sm <= 0 || ctas_per_sm > 32 || !d_sink || !fma_per_s)
+        QED_FAIL(QED_ERR_INVALID_ARG, "bad probe arguments");
+    cudaStream_t st = as_stream(stream);
+    const int grid = sm_count() * ctas_per_sm;
+    cudaEvent_t e0, e1;
+    QED_CUDA_TRY(cudaEventCreate(&e0));
+    QED_CUDA_TRY(cudaEventCreate(&e1));
+    fp64_fma_kernel<<<grid, 256, 0, st>>>(iters / 10 + 1, 0.999999, 1e-7, d_sink);  // warm-up
+    cudaEventRecord(e0, st);
+    fp64_fma_kernel<<<grid, 256, 0, st>>>(iters, 0.999999, 1e-7, d_sink);
+    cudaEventRecord(e1, st);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) QED_FAIL(QED_ERR_CUDA, "probe failed: %s", cudaGetErrorString(e));
+    *fma_per_s = (double)grid * 256.0 * kProbeChains * (double)iters / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    return QED_OK;
+}

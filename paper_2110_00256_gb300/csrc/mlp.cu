@@ -17,9 +17,8 @@ MlpView mlp_view(const qed_mlp *m, int proc)
     MlpView v;
     v.w = m->w[proc];
     v.ln_min = (float)std::log(m->chi_min[proc]);
+    v.ln_max = (float)std::log(m->chi_max[proc]);
     v.scale = (float)(2.0 / (std::log(m->chi_max[proc]) - std::log(m->chi_min[proc])));
-    v.chi_min = (float)m->chi_min[proc];
-    v.chi_max = (float)m->chi_max[proc];
     v.proc = proc;
     return v;
 }
@@ -58,7 +57,10 @@ constexpr int kTrainThreads = 128;
 constexpr int kTS = kTrainThreads + 1;  // padded sample stride of the [64][samples] buffers
 
 struct TrainSmem {
-    float w1[kMlpH * 2], b1[kMlpH], w2[kMlpH * kMlpH], b2[kMlpH], w3[kMlpH], b3;
+    alignas(8) float w1a[kMlpH];
+    alignas(8) float w1b[kMlpH];
+    alignas(8) float b1[kMlpH];
+    float w2[kMlpH * kMlpH], b2[kMlpH], w3[kMlpH], b3;
     float g[kMlpParams];       // gradient accumulator of this CTA
     float h1[kMlpH * kTS];     // bf16-rounded h1, [k][s]
     float z2[kMlpH * kTS];     // z2, then d2 = dL/dz2
@@ -77,7 +79,10 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
     const int tid = threadIdx.x;
-    for (int i = tid; i < kMlpH * 2; i += blockDim.x) S.w1[i] = __bfloat162float(v.w[kOffW1 + i]);
+    for (int i = tid; i < kMlpH; i += blockDim.x) {
+        S.w1a[i] = __bfloat162float(v.w[kOffW1 + 2 * i]);
+        S.w1b[i] = __bfloat162float(v.w[kOffW1 + 2 * i + 1]);
+    }
     for (int i = tid; i < kMlpH * kMlpH; i += blockDim.x) S.w2[i] = __bfloat162float(v.w[kOffW2 + i]);
     for (int i = tid; i < kMlpH; i += blockDim.x) {
         S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
@@ -98,25 +103,33 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
         const bool valid = i < n;
         float x1 = 0.f, x2 = 0.f, tgt = 0.f;
         if (valid) {
-            mlp_features(v, chi[i], uu[i], x1, x2);
-            if (v.proc == QED_PROC_QS) {
-                tgt = (float)(log(xi[i]) - 3.0 * log(uu[i]));
-            } else {
-                const double xm = xi[i];
-                tgt = (float)(uu[i] <= 0.5 ? xm : 1.0 - xm);  // folded fraction of the sampled lepton
-            }
+            const MlpIn in = mlp_input(v, chi[i], uu[i]);
+            x1 = in.x1, x2 = in.x2;
+            tgt = mlp_target(v.proc, xi[i], in);
         }
         S.x[0][tid] = x1;
         S.x[1][tid] = x2;
-        // forward
-        for (int k = 0; k < kMlpH; ++k)
-            S.h1[k * kTS + tid] = bf16r(gelu(fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k]))));
+        // forward, with the inference kernels' arithmetic (pairs of neurons)
+        const uint64_t x1x1 = f2(x1, x1), x2x2 = f2(x2, x2);
+        for (int k = 0; k < kMlpH; k += 2) {
+            const float2 g = f2u(layer1_pair(S.w1a, S.w1b, S.b1, k, x1x1, x2x2));
+            S.h1[k * kTS + tid] = bf16r(g.x);
+            S.h1[(k + 1) * kTS + tid] = bf16r(g.y);
+        }
         float y = S.b3;
-        for (int j = 0; j < kMlpH; ++j) {
-            float z = S.b2[j];
-            for (int k = 0; k < kMlpH; ++k) z = fmaf(S.w2[j * kMlpH + k], S.h1[k * kTS + tid], z);
-            S.z2[j * kTS + tid] = z;
-            y = fmaf(S.w3[j], gelu(z), y);
+        for (int j = 0; j < kMlpH; j += 2) {
+            float z0 = S.b2[j], z1 = S.b2[j + 1];
+            for (int k = 0; k < kMlpH; ++k) {
+                const float h = S.h1[k * kTS + tid];
+                z0 = fmaf(S.w2[j * kMlpH + k], h, z0);
+                z1 = fmaf(S.w2[(j + 1) * kMlpH + k], h, z1);
+            }
+            S.z2[j * kTS + tid] = z0;
+            S.z2[(j + 1) * kTS + tid] = z1;
+            const float2 g = f2u(gelu2(f2(z0, z1)));
+            S.q[j * kTS + tid] = g.x;
+            S.q[(j + 1) * kTS + tid] = g.y;
+            y = fmaf(S.w3[j + 1], g.y, fmaf(S.w3[j], g.x, y));
         }
         const float r = valid ? y - tgt : 0.f;
         my_loss += r * r;
@@ -124,7 +137,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
         S.dy[tid] = dy;
         for (int j = 0; j < kMlpH; ++j) {
             const float z = S.z2[j * kTS + tid];
-            S.q[j * kTS + tid] = dy * gelu(z);                    // for dW3
+            S.q[j * kTS + tid] *= dy;                             // dy h2, for dW3
             S.z2[j * kTS + tid] = dy * S.w3[j] * gelu_grad(z);    // d2
         }
         __syncthreads();
@@ -153,7 +166,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
         for (int k = 0; k < kMlpH; ++k) {
             float acc = 0.f;
             for (int j = 0; j < kMlpH; ++j) acc = fmaf(S.w2[j * kMlpH + k], S.z2[j * kTS + tid], acc);
-            const float z1 = fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k]));
+            const float z1 = fmaf(S.w1a[k], x1, fmaf(S.w1b[k], x2, S.b1[k]));
             S.q[k * kTS + tid] = acc * gelu_grad(z1);
         }
         __syncthreads();
@@ -215,7 +228,11 @@ constexpr uint32_t kTcCols = 2 * kMlpH;  // one FP32 accumulator of N = 64 colum
 struct TcSmem {
     __nv_bfloat16 b[kMlpH * kMlpH];       // W2 [n][k] (B operand, K-major)
     __nv_bfloat16 a[2][kTcTile * kMlpH];  // H1 of each group's tile [m][k] (A operand, K-major)
-    float w1[kMlpH * 2], b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    alignas(8) float w1a[kMlpH];
+    alignas(8) float w1b[kMlpH];
+    alignas(8) float b1[kMlpH];
+    alignas(8) float b2[kMlpH];
+    alignas(8) float w3[kMlpH];
     float b3;
     alignas(8) uint64_t bar[2];
     uint32_t tmem;
@@ -231,7 +248,7 @@ __device__ __forceinline__ void group_sync(int group)
     asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kTcTile) : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
+__global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
                                                                      const double *__restrict__ uu, int64_t n,
                                                                      double *__restrict__ xi)
 {
@@ -241,8 +258,9 @@ __global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, co
     for (int i = tid; i < kMlpH * kMlpH; i += kTcThreads)
         *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(S.b) + core_offset(i / kMlpH, i % kMlpH)) =
             v.w[kOffW2 + i];
-    for (int i = tid; i < kMlpH * 2; i += kTcThreads) S.w1[i] = __bfloat162float(v.w[kOffW1 + i]);
     for (int i = tid; i < kMlpH; i += kTcThreads) {
+        S.w1a[i] = __bfloat162float(v.w[kOffW1 + 2 * i]);
+        S.w1b[i] = __bfloat162float(v.w[kOffW1 + 2 * i + 1]);
         S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
         S.b2[i] = __bfloat162float(v.w[kOffB2 + i]);
         S.w3[i] = __bfloat162float(v.w[kOffW3 + i]);
@@ -269,22 +287,27 @@ __global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, co
     const uint32_t tacc = dacc + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t parity = 0;
     const int64_t stride = (int64_t)gridDim.x * 2 * kTcTile;
-    for (int64_t base = ((int64_t)blockIdx.x * 2 + grp) * kTcTile; base < n; base += stride) {
+    const int64_t base0 = ((int64_t)blockIdx.x * 2 + grp) * kTcTile;
+    // (chi, U) of the next round are loaded one round ahead, so that their
+    // latency overlaps this round's work
+    double c_next = base0 + row < n ? chi[base0 + row] : 1.0, u_next = base0 + row < n ? uu[base0 + row] : 0.5;
+    for (int64_t base = base0; base < n; base += stride) {
         const int64_t i = base + row;
         const bool valid = i < n;
-        const double c = valid ? chi[i] : 1.0, u = valid ? uu[i] : 0.5;
-        float x1, x2;
-        mlp_features(v, c, u, x1, x2);
+        const double c = c_next, u = u_next;
+        const int64_t j = i + stride;
+        c_next = j < n ? chi[j] : 1.0;
+        u_next = j < n ? uu[j] : 0.5;
+        const MlpIn in = mlp_input(v, c, u);
         // layer 1 on the CUDA cores, rounded to bf16 into row `row` of the A tile
+        const uint64_t x1x1 = f2(in.x1, in.x1), x2x2 = f2(in.x2, in.x2);
 #pragma unroll
         for (int kc = 0; kc < kMlpH / 8; ++kc) {
             uint32_t w[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int k = kc * 8 + 2 * q;
-                const float a = gelu(fmaf(S.w1[2 * k], x1, fmaf(S.w1[2 * k + 1], x2, S.b1[k])));
-                const float b = gelu(fmaf(S.w1[2 * k + 2], x1, fmaf(S.w1[2 * k + 3], x2, S.b1[k + 1])));
-                w[q] = pack_bf16(a, b);
+                const float2 g = f2u(layer1_pair(S.w1a, S.w1b, S.b1, kc * 8 + 2 * q, x1x1, x2x2));
+                w[q] = pack_bf16(g.x, g.y);
             }
             *reinterpret_cast<uint4 *>(arow + kc * 128) = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -315,17 +338,24 @@ __global__ void __launch_bounds__(kTcThreads) mlp_sample_tc_kernel(MlpView v, co
             continue;
         }
         tc_fence_after();
-        // bias, GELU and layer 3 on this thread's 64 accumulators
-        float y = S.b3;
+        // bias, GELU and layer 3 on this thread's 64 accumulators, in pairs
+        uint64_t y2 = f2(S.b3, 0.0f);
 #pragma unroll
-        for (int c0 = 0; c0 < kMlpH; c0 += 16) {
-            uint32_t r[16];
-            tc_ld16(tacc + (uint32_t)c0, r);
+        for (int c0 = 0; c0 < kMlpH; c0 += 32) {
+            uint32_t ra[16], rb[16];
+            tc_ld16(tacc + (uint32_t)c0, ra);  // two loads in flight, one wait
+            tc_ld16(tacc + (uint32_t)(c0 + 16), rb);
             tc_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) y = fmaf(S.w3[c0 + j], gelu(__uint_as_float(r[j]) + S.b2[c0 + j]), y);
+            for (int q = 0; q < 32; q += 2) {
+                const uint32_t r0 = q < 16 ? ra[q] : rb[q - 16], r1 = q < 16 ? ra[q + 1] : rb[q - 15];
+                const uint64_t b2 = *reinterpret_cast<const uint64_t *>(S.b2 + c0 + q);
+                const uint64_t w3 = *reinterpret_cast<const uint64_t *>(S.w3 + c0 + q);
+                y2 = ffma2(w3, gelu2(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2)), y2);
+            }
         }
-        if (valid) xi[i] = mlp_output(v.proc, y, u);
+        const float2 yy = f2u(y2);
+        if (valid) xi[i] = mlp_output(v.proc, yy.x + yy.y, in);
     }
     tc_fence_before();
     __syncthreads();

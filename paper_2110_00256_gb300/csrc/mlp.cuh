@@ -1,14 +1,29 @@
 // mlp.cuh -- the learned inverse-CDF sampler: a 2-64-64-1 GELU network per
-// process (QS: ln xi - 3 ln U; BW: the folded pair-split fraction), bfloat16
-// weights, FP32 accumulation, the 64x64 layer on the tensor cores
-// (mma.sync m16n8k16 bf16 -> f32).  The paper has no learned sampler: this
-// stands in for the 2-D inverse-CDF tables of §3.1 and §3.2.
+// process, bfloat16 weights, FP32 accumulation, the 64x64 layer on the tensor
+// cores.  The paper has no learned sampler: this stands in for the 2-D
+// inverse-CDF tables of §3.1 and §3.2.
+//
+// Inputs (chi, U) -> features x1 = ln chi_c scaled to [-1, 1] over the chi
+// range (chi_c = chi clamped into it), x2 = 2 U - 1 (QS) or 4 min(U, 1 - U) - 1
+// (BW).  Output maps (centred and scaled so that the network's output y is of
+// order one over the whole chi range):
+//   QS: ln(xi / (1 - xi)) = y + 3 ln U + L(chi_c),  L(chi) = ln(chi / (1 + chi))
+//       (xi ~ U^3 as U -> 0, xi scales with chi for small chi, and the logit
+//       resolves the hard end xi -> 1 in 1 - xi);
+//   BW: the folded fraction of the lepton U selects (U <= 1/2: the electron)
+//       xi_s = clamp(1/2 - w(chi_c) y, 0, 1/2),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
+//       (the pair split concentrates around 1/2 with a width ~ sqrt(3 chi / 64)
+//       for small chi).
+// Activation: GELU in its tanh form, the FP32 arithmetic in packed pairs
+// (f32x2) and the tanh on the FP16 pair (tanh.approx.f16x2, ~2^-11), the same
+// instructions in training and in every inference path.
 //
 // Parameter vector (kMlpParams floats, bf16 on the device for inference):
 // W1[64][2], b1[64], W2[64][64], b2[64], W3[64], b3.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 
@@ -22,7 +37,7 @@ constexpr int kMlpPad = 72;  // bf16 row stride of the shared 64-wide tiles (con
 // input normalisation of one process: x1 = (ln chi_c - ln_min) * scale - 1
 struct MlpView {
     const __nv_bfloat16 *w;  // kMlpParams bf16
-    float ln_min, scale, chi_min, chi_max;
+    float ln_min, ln_max, scale;
     int proc;                // QED_PROC_QS or QED_PROC_BW
 };
 
@@ -33,15 +48,63 @@ __device__ __forceinline__ float tanh_approx(float x)
     return y;
 }
 
-// gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))  (Hendrycks & Gimpel),
-// evaluated as h + h tanh(u) with h = x/2, u = x (sqrt(2/pi) + sqrt(2/pi) 0.044715 x^2):
-// six instructions, the GELUs being what bounds the network's throughput
-__device__ __forceinline__ float gelu(float x)
+// ---- packed FP32 pairs (two lanes of one 64-bit register) ------------------
+__device__ __forceinline__ uint64_t f2(float lo, float hi)
 {
-    const float u = x * fmaf(0.035677408136300125f, x * x, 0.7978845608028654f);
-    const float h = 0.5f * x;
-    return fmaf(h, tanh_approx(u), h);
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
+__device__ __forceinline__ float2 f2u(uint64_t r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// tanh of both lanes, evaluated on the FP16 pair
+__device__ __forceinline__ uint64_t tanh2(uint64_t u)
+{
+    const float2 v = f2u(u);
+    uint32_t h, t;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(v.y), "f"(v.x));  // (hi, lo)
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+    const __half2 th = *reinterpret_cast<const __half2 *>(&t);
+    return f2(__low2float(th), __high2float(th));
+}
+
+// gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))  (Hendrycks & Gimpel)
+// on both lanes: h = x/2, u = x (sqrt(2/pi) + sqrt(2/pi) 0.044715 x^2), h + h tanh(u)
+__device__ __forceinline__ uint64_t gelu2(uint64_t x)
+{
+    const uint64_t c1 = f2(0.035677408136300125f, 0.035677408136300125f);
+    const uint64_t c0 = f2(0.7978845608028654f, 0.7978845608028654f);
+    const uint64_t half = f2(0.5f, 0.5f);
+    const uint64_t u = fmul2(x, ffma2(c1, fmul2(x, x), c0));
+    const uint64_t h = fmul2(half, x);
+    return ffma2(h, tanh2(u), h);
+}
+
+// one lane of gelu2 (the same arithmetic; for scalar uses)
+__device__ __forceinline__ float gelu(float x) { return f2u(gelu2(f2(x, x))).x; }
 
 __device__ __forceinline__ float gelu_grad(float x)
 {
@@ -50,28 +113,60 @@ __device__ __forceinline__ float gelu_grad(float x)
     return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * 0.7978845608028654f * fmaf(0.134145f * x, x, 1.0f);
 }
 
-// features of one sample (see the parameter layout above)
-// (FP32 arithmetic: the network itself works to bf16 precision)
-__device__ __forceinline__ void mlp_features(const MlpView &v, double chi, double u, float &x1, float &x2)
+// ---- inputs and output map ------------------------------------------------
+// What one sample contributes besides the network: features, ln U, the output
+// map's centre (QS) or scale (BW), and whether U <= 1/2.  FP32 from the FP64
+// inputs' bits (no FP64 arithmetic): ln chi from the exponent and the leading
+// 23 mantissa bits, U truncated to FP32 (relative error < 2^-23).
+struct MlpIn {
+    float x1, x2, lnu, base;
+    bool low;
+};
+
+__device__ __forceinline__ MlpIn mlp_input(const MlpView &v, double chi, double u)
 {
-    float c = (float)chi;
-    c = c < v.chi_min ? v.chi_min : (c > v.chi_max ? v.chi_max : c);
-    x1 = (logf(c) - v.ln_min) * v.scale - 1.0f;
-    const double up = v.proc == QED_PROC_QS ? u : 2.0 * (u < 1.0 - u ? u : 1.0 - u);
-    x2 = (float)(2.0 * up - 1.0);
+    MlpIn r;
+    const unsigned long long bc = (unsigned long long)__double_as_longlong(chi);
+    const int e = (int)((bc >> 52) & 0x7ffu) - 1023;
+    const float mc = __uint_as_float(0x3f800000u | (uint32_t)((bc >> 29) & 0x7fffffu));  // [1, 2)
+    float lc = fmaf((float)e, 0.6931471805599453f, __logf(mc));
+    lc = fminf(fmaxf(lc, v.ln_min), v.ln_max);
+    if (e == 1024 || (long long)bc < 0) lc = __int_as_float(0x7fc00000);  // NaN, inf or negative: NaN out
+    r.x1 = fmaf(lc - v.ln_min, v.scale, -1.0f);
+    const unsigned long long bu = (unsigned long long)__double_as_longlong(u);
+    const uint32_t eu = (uint32_t)((bu >> 52) & 0x7ffu);
+    float uf = __uint_as_float(((eu - 896u) << 23) | (uint32_t)((bu >> 29) & 0x7fffffu));
+    if (eu <= 896u) uf = 1e-38f;  // U below FP32's normal range (U = 0 is not a valid draw)
+    r.low = bu <= 0x3FE0000000000000ull;  // U <= 1/2, decided on the FP64 draw
+    r.lnu = __logf(uf);
+    if (v.proc == QED_PROC_QS) {
+        r.x2 = fmaf(2.0f, uf, -1.0f);
+        r.base = lc - __logf(1.0f + __expf(lc));
+    } else {
+        r.x2 = fmaf(4.0f, r.low ? uf : 1.0f - uf, -1.0f);
+        r.base = 0.5f * rsqrtf(fmaf(5.333333333333333f, __expf(-lc), 1.0f));
+    }
+    return r;
 }
 
-// network output -> sampled xi.  QS: xi = exp(min(y + 3 ln U, 0)).  BW: the
-// electron's fraction chi_- / chi_g, from the folded fraction clamp(y, 0, 1/2)
-// of the lepton that U selects (U <= 1/2: electron), as in the table path.
-__device__ __forceinline__ double mlp_output(int proc, float y, double u)
+// network output -> sampled xi (QS: chi_gamma / chi; BW: the electron's chi_- / chi_g)
+__device__ __forceinline__ double mlp_output(int proc, float y, const MlpIn &in)
 {
     if (proc == QED_PROC_QS) {
-        const float l = fmaf(3.0f, logf((float)u), y);
-        return (double)expf(l > 0.0f ? 0.0f : l);
+        const float l = fmaf(3.0f, in.lnu, y + in.base);
+        return (double)(1.0f / (1.0f + __expf(-l)));
     }
-    double xs = y < 0.0f ? 0.0 : (y > 0.5f ? 0.5 : (double)y);
-    return u <= 0.5 ? xs : 1.0 - xs;
+    float xs = fmaf(-in.base, y, 0.5f);
+    xs = xs < 0.0f ? 0.0f : (xs > 0.5f ? 0.5f : xs);
+    return (double)(in.low ? xs : 1.0f - xs);
+}
+
+// the output y whose map gives xi (the training target of a sample)
+__device__ __forceinline__ float mlp_target(int proc, double xi, const MlpIn &in)
+{
+    if (proc == QED_PROC_QS) return (float)(log(xi) - log1p(-xi)) - fmaf(3.0f, in.lnu, in.base);
+    const float xs = (float)(in.low ? xi : 1.0 - xi);
+    return (0.5f - xs) / in.base;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -80,11 +175,26 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// layer 1 for neurons (k, k + 1), k even: gelu(W1 x + b1) on both lanes.
+// w1a / w1b: the coefficients of x1 / x2 as contiguous float arrays.
+__device__ __forceinline__ uint64_t layer1_pair(const float *w1a, const float *w1b, const float *b1, int k,
+                                                uint64_t x1x1, uint64_t x2x2)
+{
+    const uint64_t a = *reinterpret_cast<const uint64_t *>(w1a + k);
+    const uint64_t b = *reinterpret_cast<const uint64_t *>(w1b + k);
+    const uint64_t c = *reinterpret_cast<const uint64_t *>(b1 + k);
+    return gelu2(ffma2(a, x1x1, ffma2(b, x2x2, c)));
+}
+
 // Stage one network's weights in shared memory: W2 as bf16 rows [n][k] with
 // stride kMlpPad, the small layers as float.  All threads of the CTA call it.
 struct MlpSmem {
     __nv_bfloat16 w2[kMlpH * kMlpPad];
-    float w1[kMlpH * 2], b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    alignas(8) float w1a[kMlpH];
+    alignas(8) float w1b[kMlpH];
+    alignas(8) float b1[kMlpH];
+    alignas(8) float b2[kMlpH];
+    alignas(8) float w3[kMlpH];
     float b3;
 };
 
@@ -92,7 +202,10 @@ __device__ __forceinline__ void mlp_stage(MlpSmem &s, const __nv_bfloat16 *w)
 {
     for (int i = threadIdx.x; i < kMlpH * kMlpH; i += blockDim.x)
         s.w2[(i / kMlpH) * kMlpPad + (i % kMlpH)] = w[kOffW2 + i];
-    for (int i = threadIdx.x; i < kMlpH * 2; i += blockDim.x) s.w1[i] = __bfloat162float(w[kOffW1 + i]);
+    for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
+        s.w1a[i] = __bfloat162float(w[kOffW1 + 2 * i]);
+        s.w1b[i] = __bfloat162float(w[kOffW1 + 2 * i + 1]);
+    }
     for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
         s.b1[i] = __bfloat162float(w[kOffB1 + i]);
         s.b2[i] = __bfloat162float(w[kOffB2 + i]);
@@ -110,11 +223,11 @@ __device__ __forceinline__ float mlp_forward_warp(const MlpSmem &s, __nv_bfloat1
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // layer 1 on the CUDA cores, rounded to bf16 into the A tile (row = sample)
     uint32_t *row = reinterpret_cast<uint32_t *>(h1 + lane * kMlpPad);
+    const uint64_t x1x1 = f2(x1, x1), x2x2 = f2(x2, x2);
 #pragma unroll 8
     for (int k = 0; k < kMlpH; k += 2) {
-        const float a = gelu(fmaf(s.w1[2 * k], x1, fmaf(s.w1[2 * k + 1], x2, s.b1[k])));
-        const float b = gelu(fmaf(s.w1[2 * k + 2], x1, fmaf(s.w1[2 * k + 3], x2, s.b1[k + 1])));
-        row[k >> 1] = pack_bf16(a, b);
+        const float2 g = f2u(layer1_pair(s.w1a, s.w1b, s.b1, k, x1x1, x2x2));
+        row[k >> 1] = pack_bf16(g.x, g.y);
     }
     __syncwarp();
     // layer 2 on the tensor cores: Z[32 x 64] = H1[32 x 64] W2^T, in two halves of
@@ -162,10 +275,12 @@ __device__ __forceinline__ float mlp_forward_warp(const MlpSmem &s, __nv_bfloat1
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const int n0 = half * 32 + nt * 8 + 2 * t;
-                part[mt][0] += s.w3[n0] * gelu(acc[mt][nt][0] + s.b2[n0]) +
-                               s.w3[n0 + 1] * gelu(acc[mt][nt][1] + s.b2[n0 + 1]);
-                part[mt][1] += s.w3[n0] * gelu(acc[mt][nt][2] + s.b2[n0]) +
-                               s.w3[n0 + 1] * gelu(acc[mt][nt][3] + s.b2[n0 + 1]);
+                const uint64_t b2 = *reinterpret_cast<const uint64_t *>(s.b2 + n0);
+                const uint64_t w3 = *reinterpret_cast<const uint64_t *>(s.w3 + n0);
+                const float2 ga = f2u(fmul2(w3, gelu2(fadd2(f2(acc[mt][nt][0], acc[mt][nt][1]), b2))));
+                const float2 gb = f2u(fmul2(w3, gelu2(fadd2(f2(acc[mt][nt][2], acc[mt][nt][3]), b2))));
+                part[mt][0] += ga.x + ga.y;
+                part[mt][1] += gb.x + gb.y;
             }
     }
     // reduce the layer-3 partial sums over the four lanes of a group

@@ -47,6 +47,20 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// non-blocking test of the same (mbarrier.test_wait: no suspended wait in hardware)
+__device__ __forceinline__ bool mbar_peek(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // bounded wait for the phase of parity `parity`; false if it gave up
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {

@@ -179,9 +179,266 @@ __global__ void __launch_bounds__(256) table_rows_kernel(const __grid_constant__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact inverse CDF, no table (the learned sampler's training targets).  Per chi
+// row, the cumulative integral of the spectrum on a fine grid and its density
+// at the nodes; per draw, the bracketing interval by binary search, a first
+// guess from the cubic Hermite interpolant of the cumulative integral on that
+// interval (value and slope at both nodes), then Newton steps on the partial
+// integral from the interval's left node (Gauss-Legendre, 8 points).
+// Grid variables (both smooth in them over the whole range):
+//   QS: v = ln(xi / (1 - xi)) on [ln 1e-12, -ln 1e-12] in kExactIntervals - 1
+//       equal intervals, plus [ln 1e-12 - 100, ln 1e-12] below (where P follows
+//       its xi^(1/3) law; tanh-sinh there); the density is S(chi, xi) (1 - xi),
+//       which resolves both the soft end and the cut-off at 1 - xi ~ 1/chi;
+//   BW: v = ln xi on [ln 1e-12, ln 1/2] in kExactIntervals equal intervals,
+//       density xi times the bracket of Eq. (t_func_0), normalised to P(1/2) = 1.
+// ---------------------------------------------------------------------------
+constexpr int kExactIntervals = 1024;
+constexpr double kExactLo = -27.631021115928547;  // ln 1e-12
+
+struct GaussLegendre8 {
+    double x[8], w[8];  // nodes and weights on [-1, 1]
+};
+
+// density in v of the QS photon number spectrum: S(chi, xi) (1 - xi)
+__device__ double qs_density_v(double chi, double v)
+{
+    const double e = exp(-fabs(v));
+    const double xi = v >= 0.0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+    const double om = v >= 0.0 ? e / (1.0 + e) : 1.0 / (1.0 + e);  // 1 - xi without cancellation
+    if (!(om > 0.0) || !(xi > 0.0)) return 0.0;
+    const double Y = (2.0 / 3.0) * xi / (chi * om);
+    if (Y > 745.0) return 0.0;
+    double ia, kb;
+    bessel_scaled(Y, 5.0 / 3.0, 2.0 / 3.0, ia, kb);
+    return (0.27566444771089600 /* sqrt(3) / (2 pi) */) * xi * om * exp(-Y) * (ia + xi * xi / om * kb);
+}
+
+// density in v = ln xi of the BW split: xi times the bracket
+__device__ double bw_density_v(double chi, double v)
+{
+    const double xi = exp(v);
+    return xi * bw_integrand(chi, xi);
+}
+
+__device__ __forceinline__ double exact_density(bool qs, double chi, double v)
+{
+    return qs ? qs_density_v(chi, v) : bw_density_v(chi, v);
+}
+
+// node j of the grid (j = 0 .. kExactIntervals)
+__device__ __forceinline__ double exact_node(bool qs, int j)
+{
+    if (qs) {
+        if (j == 0) return kExactLo - kQsBelow;
+        return kExactLo + (j - 1) * (-2.0 * kExactLo) / (kExactIntervals - 1);
+    }
+    return kExactLo + j * (-0.6931471805599453 - kExactLo) / kExactIntervals;
+}
+
+__device__ double gl8(const GaussLegendre8 &g, bool qs, double chi, double a, double b)
+{
+    const double c = 0.5 * (a + b), h = 0.5 * (b - a);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += g.w[i] * exact_density(qs, chi, fma(h, g.x[i], c));
+    return h * s;
+}
+
+// The QS interval below the grid (v from ln 1e-12 - 100 to ln 1e-12): there the
+// density grows like e^{v/3} (the xi^(1/3) law of P), so it is integrated in
+// w = e^{v/3}, where the integrand 3 density / w is nearly constant (8-point
+// Gauss-Legendre on [w(a), w(v)]).
+__device__ double gl8_below(const GaussLegendre8 &g, double chi, double a, double v)
+{
+    const double wa = exp(a / 3.0), wb = exp(v / 3.0);
+    const double c = 0.5 * (wa + wb), h = 0.5 * (wb - wa);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double w = fma(h, g.x[i], c);
+        s += g.w[i] * 3.0 * qs_density_v(chi, 3.0 * log(w)) / w;
+    }
+    return h * s;
+}
+
+constexpr int kExactRowStride = 2 * (kExactIntervals + 1) + 1;  // P[0..M], p[0..M], total
+
+// one CTA per chi row: P at the nodes (P_0 = 0 .. P_M = 1), the density p at
+// the nodes divided by the total, then the total
+__global__ void __launch_bounds__(256) exact_rows_kernel(int qs, const double *__restrict__ chi_rows,
+                                                          double *__restrict__ work, GaussLegendre8 g)
+{
+    __shared__ double acc[kExactIntervals];
+    const double chi = chi_rows[blockIdx.x];
+    double *out = work + (size_t)blockIdx.x * kExactRowStride;
+    if (qs && threadIdx.x == 0) acc[0] = gl8_below(g, chi, exact_node(true, 0), exact_node(true, 1));
+    for (int j = threadIdx.x + (qs ? 1 : 0); j < kExactIntervals; j += blockDim.x)
+        acc[j] = gl8(g, qs, chi, exact_node(qs, j), exact_node(qs, j + 1));
+    for (int j = threadIdx.x; j <= kExactIntervals; j += blockDim.x)
+        out[kExactIntervals + 1 + j] = exact_density(qs, chi, exact_node(qs, j));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int j = 0; j < kExactIntervals; ++j) tot += acc[j];
+        double c = 0.0;
+        out[0] = 0.0;
+        for (int j = 0; j < kExactIntervals; ++j) {
+            c += acc[j];
+            out[j + 1] = tot > 0.0 ? c / tot : 0.0;
+        }
+        out[kExactIntervals] = 1.0;
+        out[2 * (kExactIntervals + 1)] = tot;
+    }
+    __syncthreads();
+    const double tot = out[2 * (kExactIntervals + 1)];
+    for (int j = threadIdx.x; j <= kExactIntervals; j += blockDim.x)
+        out[kExactIntervals + 1 + j] = tot > 0.0 ? out[kExactIntervals + 1 + j] / tot : 0.0;
+}
+
+__global__ void __launch_bounds__(128) exact_draw_kernel(int qs, const double *__restrict__ chi_rows,
+                                                          const double *__restrict__ work, int64_t m, int64_t k,
+                                                          const double *__restrict__ uu, double *__restrict__ xi,
+                                                          GaussLegendre8 g)
+{
+    const int64_t n = m * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / k;
+        const double chi = chi_rows[row];
+        const double *P = work + (size_t)row * kExactRowStride;
+        const double *D = P + kExactIntervals + 1;
+        const double tot = P[2 * (kExactIntervals + 1)];
+        double u = uu[i];
+        u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+        const double r = qs ? u : 2.0 * (u < 1.0 - u ? u : 1.0 - u);
+        double v;
+        if (!(tot > 0.0) || r >= 1.0) {
+            v = qs ? 1e300 : -0.6931471805599453;
+        } else if (r <= 0.0) {
+            v = -1e300;
+        } else {
+            int lo = 0, hi = kExactIntervals;  // j: P_j <= r < P_{j+1}
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (P[mid] <= r) lo = mid; else hi = mid;
+            }
+            const int j = lo;
+            const double a = exact_node(qs, j), b = exact_node(qs, j + 1), L = b - a;
+            const double P0 = P[j], P1 = P[j + 1];
+            if (qs && j == 0) {
+                // below the grid: the xi^(1/3) law as the first guess, Newton on ln P
+                v = b + 3.0 * (log(r) - log(P1));
+                v = v < a ? a : (v > b ? b : v);
+                for (int it = 0; it < 8; ++it) {
+                    const double F = P0 + gl8_below(g, chi, a, v) / tot;
+                    const double f = exact_density(true, chi, v) / tot;
+                    if (!(F > 0.0) || !(f > 0.0)) break;
+                    double vn = v - (log(F) - log(r)) * F / f;
+                    vn = vn < a ? a : (vn > b ? b : vn);
+                    const double dv = fabs(vn - v);
+                    v = vn;
+                    if (dv < 1e-13) break;
+                }
+            } else {
+                // cubic Hermite of P on t in [0, 1]: P(t) = P0 + ... with slopes L p_j, L p_{j+1};
+                // its inverse by Newton from the linear guess
+                const double m0 = L * D[j], m1 = L * D[j + 1], dP = P1 - P0;
+                double t = dP > 0.0 ? (r - P0) / dP : 0.5;
+                for (int it = 0; it < 6; ++it) {
+                    const double t2 = t * t, t3 = t2 * t;
+                    const double h = P0 * (2 * t3 - 3 * t2 + 1) + m0 * (t3 - 2 * t2 + t) + P1 * (-2 * t3 + 3 * t2) +
+                                     m1 * (t3 - t2);
+                    const double dh = P0 * (6 * t2 - 6 * t) + m0 * (3 * t2 - 4 * t + 1) + P1 * (-6 * t2 + 6 * t) +
+                                      m1 * (3 * t2 - 2 * t);
+                    if (!(dh > 0.0)) break;
+                    double tn = t - (h - r) / dh;
+                    tn = tn < 0.0 ? 0.0 : (tn > 1.0 ? 1.0 : tn);
+                    t = tn;
+                }
+                v = a + L * t;
+                // Newton on the partial integral (the cumulative integral itself)
+                for (int it = 0; it < 4; ++it) {
+                    const double F = P0 + gl8(g, qs, chi, a, v) / tot;
+                    const double f = exact_density(qs, chi, v) / tot;
+                    if (!(f > 0.0)) break;
+                    double vn = v - (F - r) / f;
+                    vn = vn < a ? a : (vn > b ? b : vn);
+                    const double dv = fabs(vn - v);
+                    v = vn;
+                    if (dv < 1e-7 * L) break;  // the next correction is ~(dv / L)^2 of this one
+                }
+            }
+        }
+        double out;
+        if (qs) {
+            const double e = exp(-fabs(v));
+            out = v >= 0.0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+        } else {
+            out = exp(v);
+            out = out > 0.5 ? 0.5 : out;
+            out = (u <= 0.5) ? out : 1.0 - out;
+        }
+        xi[i] = out;
+    }
+}
+
+// Gauss-Legendre nodes and weights (Newton's method on the three-term recurrence)
+static GaussLegendre8 gauss_legendre8()
+{
+    GaussLegendre8 g;
+    const int n = 8;
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1, p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        g.x[i] = x;
+        g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    return g;
+}
+
 }  // namespace qed
 
 using namespace qed;
+
+extern "C" qed_status qed_exact_sample(qed_process proc, const double *d_chi, int64_t m, const double *d_u,
+                                       int64_t k, double *d_xi, double *d_work, int64_t work_capacity, void *stream)
+{
+    clear_error();
+    if (proc != QED_PROC_QS && proc != QED_PROC_BW) QED_FAIL(QED_ERR_INVALID_ARG, "bad process %d", (int)proc);
+    if (m < 0 || k < 0) QED_FAIL(QED_ERR_INVALID_ARG, "negative sizes");
+    if (m == 0 || k == 0) return QED_OK;
+    if (!d_chi || !d_u || !d_xi || !d_work) QED_FAIL(QED_ERR_INVALID_ARG, "a device array is NULL");
+    if (m > (int64_t)1 << 31 || k > ((int64_t)1 << 40) / m) QED_FAIL(QED_ERR_INVALID_ARG, "too many draws");
+    if (work_capacity < QED_EXACT_WORK(m))
+        QED_FAIL(QED_ERR_INVALID_ARG, "d_work holds %lld doubles, %lld needed", (long long)work_capacity,
+                 (long long)QED_EXACT_WORK(m));
+    static_assert(QED_EXACT_WORK(1) == kExactRowStride, "work layout");
+    static const GaussLegendre8 gl = gauss_legendre8();
+    cudaStream_t st = as_stream(stream);
+    const int qs = proc == QED_PROC_QS;
+    exact_rows_kernel<<<(unsigned)m, 256, 0, st>>>(qs, d_chi, d_work, gl);
+    QED_LAUNCH_CHECK();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t blocks = (m * k + 127) / 128;
+    const int g = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
+    exact_draw_kernel<<<g, 128, 0, st>>>(qs, d_chi, d_work, m, k, d_u, d_xi, gl);
+    QED_LAUNCH_CHECK();
+    return QED_OK;
+}
 
 extern "C" qed_status qed_tables_generate(const qed_table_params *params, qed_tables **out, void *stream)
 {

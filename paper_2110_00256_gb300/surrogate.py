@@ -1,10 +1,10 @@
 """Training and evaluation of the learned inverse-CDF sampler on the GPU.
 
-Training data: (chi, U, xi) with chi log-uniform over the table range, U uniform
-in (0, 1) (both from a seeded torch generator on the device), and xi the FP64
-inverse-CDF sample of the same (chi, U) through a fine FP64 table made by
-qed_tables_generate (the table generator is the reference the network learns).
-Every step of the training runs in libqed's kernels (forward, backward, Adam).
+Training data: (chi, U, xi) with chi log-uniform over the table range (drawn
+as `rows` distinct values, each with its share of the draws), U uniform in
+(0, 1), and xi the exact inverse CDF of the same (chi, U) computed on the GPU
+(qed_exact_sample: FP64 quadrature of the spectra, no table).  Every step of
+the training runs in libqed's kernels (forward, backward, Adam).
 """
 from __future__ import annotations
 
@@ -17,23 +17,36 @@ import torch
 from . import api
 
 
-def make_data(tables: api.Tables, proc: int, n: int, seed: int, device="cuda"):
-    """n training samples (chi, U, xi) on the device."""
+def chi_range(tables: api.Tables, proc: int):
     p = tables.params
     ax = p.qs if proc == api.QED_PROC_QS else p.bw
+    return ax.chi_min, ax.chi_max
+
+
+def make_data(tables: api.Tables, proc: int, n: int, seed: int, rows: int = 16384, device="cuda"):
+    """n training samples (chi, U, xi) on the device, xi from the exact inverse
+    CDF; chi takes `rows` log-uniform values (n // rows draws each), shuffled."""
+    lo, hi = (math.log(v) for v in chi_range(tables, proc))
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
-    chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device=device, dtype=torch.float64))
-    u = torch.rand(n, generator=g, device=device, dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
-    xi = api.qed_table_sample(tables, proc, api.QED_F64, chi, u)
-    return chi, u, xi
+    rows = max(1, min(rows, n))
+    k = max(1, n // rows)
+    chi_rows = torch.exp(lo + (hi - lo) * torch.rand(rows, generator=g, device=device, dtype=torch.float64))
+    u = torch.rand(rows * k, generator=g, device=device, dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
+    # sorted within each chi row: neighbouring threads of the exact sampler then
+    # take neighbouring intervals (similar work)
+    u = torch.sort(u.view(rows, k), dim=1).values.reshape(-1)
+    xi = api.qed_exact_sample(proc, chi_rows, u)
+    chi = chi_rows.repeat_interleave(k)
+    perm = torch.randperm(rows * k, generator=g, device=device)
+    return chi[perm], u[perm], xi[perm]
 
 
 def train(mlp: api.Mlp, data_tables: api.Tables, proc: int, n_samples: int = 10_000_000, epochs: int = 6,
           batch: int = 65536, lr: float = 3e-3, lr_final: float = 1e-4, seed: int = 1, log_every: int = 0):
     """Train one network; returns the loss history (one value per logged step)."""
     chi, u, xi = make_data(data_tables, proc, n_samples, seed)
+    n_samples = chi.numel()  # (a whole number of draws per chi value)
     g = torch.Generator(device=chi.device)
     g.manual_seed(seed + 1)
     steps = epochs * ((n_samples + batch - 1) // batch)
@@ -66,26 +79,29 @@ def ks_distance(a: torch.Tensor, b: torch.Tensor) -> float:
     return float((fa - fb).abs().max().item())
 
 
-def compare(mlp: api.Mlp, tables: api.Tables, proc: int, n: int = 1_000_000, seed: int = 99, bins: int = 5,
-            prec: int = api.QED_F32):
-    """KS distance between network samples and table samples of the same (chi, U),
-    overall and in log-chi bins; also the KS of the per-bin xi distributions."""
-    p = tables.params
-    ax = p.qs if proc == api.QED_PROC_QS else p.bw
-    gdev = torch.Generator(device="cuda")
-    gdev.manual_seed(seed)
-    lo, hi = math.log(ax.chi_min), math.log(ax.chi_max)
-    t = torch.rand(n, generator=gdev, device="cuda", dtype=torch.float64)
-    chi = torch.exp(lo + (hi - lo) * t)
-    u = torch.rand(n, generator=gdev, device="cuda", dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
-    xm = mlp.sample(proc, chi, u)
-    xt = api.qed_table_sample(tables, proc, prec, chi, u)
+def compare(sampler, tables: api.Tables, proc: int, n: int = 1_000_000, seed: int = 99, bins: int = 5,
+            rows: int = 2000):
+    """KS distance between a sampler's xi and the exact inverse CDF's on the
+    same (chi, U), overall and in `bins` equal log-chi bins of the table range.
+    `sampler(chi, u)` returns xi on the device (QS chi_gamma/chi, BW the
+    electron's fraction)."""
+    lo, hi = (math.log(v) for v in chi_range(tables, proc))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    k = max(1, n // rows)
+    t = (torch.arange(rows, device="cuda", dtype=torch.float64) + torch.rand(rows, generator=g, device="cuda",
+                                                                             dtype=torch.float64)) / rows
+    chi_rows = torch.exp(lo + (hi - lo) * t)
+    u = torch.rand(rows * k, generator=g, device="cuda", dtype=torch.float64).clamp_(1e-15, 1.0 - 1e-15)
+    xe = api.qed_exact_sample(proc, chi_rows, u)
+    chi = chi_rows.repeat_interleave(k)
+    xs = sampler(chi, u)
     key = (lambda v: torch.log(v)) if proc == api.QED_PROC_QS else (lambda v: v)
-    out = {"overall": ks_distance(key(xm), key(xt)), "bins": []}
-    edges = torch.linspace(0, 1, bins + 1, dtype=torch.float64)
+    out = {"overall": ks_distance(key(xs), key(xe)), "bins": []}
+    tt = t.repeat_interleave(k)
     for i in range(bins):
-        m = (t >= edges[i].item()) & (t < edges[i + 1].item())
-        out["bins"].append(ks_distance(key(xm[m]), key(xt[m])))
+        m = (tt >= i / bins) & (tt < (i + 1) / bins)
+        out["bins"].append(ks_distance(key(xs[m]), key(xe[m])))
     return out
 
 

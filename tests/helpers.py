@@ -218,7 +218,8 @@ def margin_ids(ot, host64, dt, tol, seed, step, cuts=(0.0, 0.0)):
         tn, chi, rate, f = oracle.evolve(proc, ot, host64[k], dt, cuts[proc])
         b = tau_bound(ot, proc, host64[k], chi, rate, dt, tol)
         near_cut = np.abs(chi - cuts[proc]) <= 1e-9 * cuts[proc]
-        for pid in host64[k]["id"][(np.abs(tn) <= b) | near_cut].tolist():
+        # (removed photons, tau = +inf, take no decision)
+        for pid in host64[k]["id"][np.isfinite(tn) & ((np.abs(tn) <= b) | near_cut)].tolist():
             out.add(pid)
             out |= set(oracle.child_ids(seed, pid, step))
     return out

@@ -51,12 +51,15 @@ def _host_patches(sizes, seed, tau_scale=3e-4, positions=False):
 
 
 def _device_patches(api, host, prec, positions=False):
+    # room for every event: which events run when a destination fills up depends
+    # on the order of the firing lists, which differs between launch forms
     out = []
     for h in host:
         p = {}
+        big = 8 * max(len(h[k]["px"]) for k in SPECIES) + 64
         for k in SPECIES:
             n = len(h[k]["px"])
-            b = api.SpeciesBuffers(3 * n + 64, prec, positions=positions)
+            b = api.SpeciesBuffers(n + big, prec, positions=positions)
             if n:
                 b.set(h[k])
             p[k] = b

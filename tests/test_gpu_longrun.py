@@ -226,21 +226,26 @@ def test_full_qs_bw_1000_steps(api, setup):
         differ += int(np.sum(np.max(np.abs(p32 - p64), axis=1) > 1e-5 * scale))
     frac = differ / (2 * N)
     print(f"FP32 vs FP64 over {STEPS} steps: primaries with a different history: {differ} ({frac:.2e})")
+    # the tight, correlated check: a history differs only where an FP32 decision
+    # fell within the FP32 rounding of the threshold (and then its descendants differ)
     assert frac < 5e-3
+    # counts, chi distribution of the events and spectra: within 5 standard
+    # deviations of independent Poisson counts (conservative for these
+    # correlated runs; one diverging cascade can move hundreds of events)
     for key in ("qs_events", "bw_events", "photons_kept", "pairs"):
         a, b = r32["stats"][key], r64["stats"][key]
         print(f"  {key}: FP32 {a}  FP64 {b}  rel diff {(a - b) / b:+.2e}")
-        assert abs(a - b) <= 2e-3 * b + 10, key
+        assert abs(a - b) <= 5.0 * np.sqrt(a + b), key
     cs32 = np.cumsum(r32["per_step"][:, [0, 1]], axis=0)
     cs64 = np.cumsum(r64["per_step"][:, [0, 1]], axis=0)
-    assert np.all(np.abs(cs32 - cs64) <= 2e-3 * cs64 + 10)
+    assert np.all(np.abs(cs32 - cs64) <= 5.0 * np.sqrt(cs32 + cs64 + 1))
     for key in ("qs", "bw"):
         h32 = np.histogram(r32["fire_chi"][key], CHI_EDGES)[0]
         h64 = np.histogram(r64["fire_chi"][key], CHI_EDGES)[0]
-        assert np.all(np.abs(h32 - h64) <= 5e-3 * h64 + 10), (key, h32, h64)
+        assert np.all(_poisson_close(h32, 1.0, h64, 1.0)), (key, h32, h64)
     s32, s64 = _secondary_spectra(f32), _secondary_spectra(f64)
     for a, b in zip(s32, s64):
-        assert np.all(np.abs(a - b) <= 1e-2 * b + 10), (a, b)
+        assert np.all(_poisson_close(a, 1.0, b, 1.0)), (a, b)
 
     # 3. both against the oracle's subsample, statistically
     for r in (r64, r32):

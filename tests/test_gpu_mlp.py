@@ -48,18 +48,25 @@ def test_forward_matches_oracle(api, tables, proc):
     cmin, cmax = _ranges(api, tables, proc)
     X = omlp.features(proc, chi, u, cmin, cmax)
     y_ref, _ = omlp.forward(theta, X, round_bf16=True)
-    if proc == 0:
-        y_gpu = np.log(xi) - 3 * np.log(u)
-        ok = y_ref + 3 * np.log(u) < -1e-3  # outside the clamp at xi = 1
-    else:
-        xs = np.where(u <= 0.5, xi, 1 - xi)
-        y_gpu = xs
-        ok = (y_ref > 1e-3) & (y_ref < 0.5 - 1e-3)
+    y_gpu, ok = _y_of(proc, xi, chi, u, y_ref, cmin, cmax)
     d = np.abs(y_gpu[ok] - y_ref[ok])
-    # tanh.approx (|rel err| < 2^-10.99) and bf16 ties of h1 that flip between the
-    # FP32 and FP64 evaluations bound the difference
+    # the FP16 tanh (~2^-11), FP32 features and bf16 ties of h1 that flip between
+    # the FP32 and FP64 evaluations bound the difference
     assert ok.sum() > 1000
     assert np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
+
+
+def _y_of(proc, xi, chi, u, y_ref, cmin, cmax):
+    """The network output that the GPU's xi implies (the inverse of the output
+    map), and where the map is not clamped by the reference output."""
+    y_gpu = omlp.targets(proc, chi, u, xi, cmin, cmax)
+    cs = omlp.centre_scale(proc, chi, cmin, cmax)
+    if proc == 0:
+        ok = (xi > 1e-30) & (xi < 1 - 1e-5)  # where the FP32 output keeps 1 - xi to 1e-2 or better
+    else:
+        xs = 0.5 - cs * y_ref
+        ok = (xs > 1e-3) & (xs < 0.5 - 1e-3)
+    return y_gpu, ok
 
 
 def _forward_error(api, tables, m, proc, chi, u):
@@ -67,10 +74,7 @@ def _forward_error(api, tables, m, proc, chi, u):
     xi = m.sample(proc, torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
     cmin, cmax = _ranges(api, tables, proc)
     y_ref, _ = omlp.forward(theta, omlp.features(proc, chi, u, cmin, cmax), round_bf16=True)
-    if proc == 0:
-        y_gpu, ok = np.log(xi) - 3 * np.log(u), y_ref + 3 * np.log(u) < -1e-3
-    else:
-        y_gpu, ok = np.where(u <= 0.5, xi, 1 - xi), (y_ref > 1e-3) & (y_ref < 0.5 - 1e-3)
+    y_gpu, ok = _y_of(proc, xi, chi, u, y_ref, cmin, cmax)
     return xi, np.abs(y_gpu[ok] - y_ref[ok])
 
 
@@ -102,8 +106,7 @@ def test_gradients_match_oracle(api, tables, proc):
     g = g.cpu().numpy().astype(np.float64)
     cmin, cmax = _ranges(api, tables, proc)
     X = omlp.features(proc, chi, u, cmin, cmax)
-    t = omlp.targets(proc, u, xi.cpu().numpy()) if proc == 0 else \
-        np.where(u <= 0.5, xi.cpu().numpy(), 1 - xi.cpu().numpy())
+    t = omlp.targets(proc, chi, u, xi.cpu().numpy(), cmin, cmax)
     l_ref, g_ref = omlp.loss_and_grad(theta, X, t, round_bf16=True)
     assert float(loss.item()) == pytest.approx(l_ref, rel=1e-2)
     segs = {"W1": (0, 128), "b1": (128, 192), "W2": (192, 4288), "b2": (4288, 4352), "W3": (4352, 4416),
@@ -111,19 +114,6 @@ def test_gradients_match_oracle(api, tables, proc):
     for name, (a, b) in segs.items():
         rel = np.linalg.norm(g[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-12)
         assert rel < 2e-2, (name, rel)
-
-
-@pytest.mark.parametrize("proc", [0, 1])
-def test_training_learns_the_tables(api, tables, proc):
-    from paper_2110_00256_gb300 import surrogate
-    fine = api.qed_tables_generate(api.table_params(qs_n_chi=256, qs_n_xi=512, bw_n_chi=256, bw_n_xi=512))
-    m = api.Mlp(fine, seed=31 + proc)
-    before = surrogate.compare(m, fine, proc, n=200_000, prec=api.QED_F64)["overall"]
-    rep = surrogate.train(m, fine, proc, n_samples=1_000_000, epochs=8, batch=32768, log_every=10)
-    h = rep["history"]
-    assert h[-1] < 0.2 * h[0]
-    after = surrogate.compare(m, fine, proc, n=200_000, prec=api.QED_F64)
-    assert after["overall"] < 0.5 * before and after["overall"] < 0.05, (before, after)
 
 
 def test_substep_with_learned_sampler(api, tables):

@@ -64,10 +64,27 @@ def test_adam_first_step_is_signed_lr():
 def test_output_maps():
     u = np.array([1e-6, 0.3, 0.7, 0.999])
     y = np.array([0.2, -1.0, 0.4, 0.0])
-    qs = mlp.output(0, y, u)
-    assert np.all(qs <= 1.0) and np.allclose(np.log(qs[:3]), np.minimum(y[:3] + 3 * np.log(u[:3]), 0.0))
-    bw = mlp.output(1, np.array([0.2, 0.7, -0.1, 0.3]), u)
-    assert np.allclose(bw, [0.2, 0.5, 0.0, 0.3])
+    chi = np.array([1e-4, 1.0, 3.0, 5e3])  # the first and last outside [1e-3, 1e3]: clamped
+    qs = mlp.output(0, y, chi, u, 1e-3, 1e3)
+    L = np.log(np.clip(chi, 1e-3, 1e3) / (1 + np.clip(chi, 1e-3, 1e3)))
+    assert L[1] == pytest.approx(-math.log(2.0)) and L[0] == pytest.approx(math.log(1e-3 / 1.001))
+    assert np.all(qs < 1.0) and np.allclose(np.log(qs / (1 - qs)), y + 3 * np.log(u) + L)
+    # the map inverts the targets
+    t = mlp.targets(0, chi, u, qs, 1e-3, 1e3)
+    assert np.allclose(t, y)
+    # BW: w(chi) -> sqrt(3 chi / 64) for small chi, 1/2 for large
+    w = mlp.centre_scale(1, np.array([1e-6, 1e9]), 1e-6, 1e9)
+    assert w[0] == pytest.approx(math.sqrt(3e-6 / 64), rel=1e-6) and w[1] == pytest.approx(0.5, rel=1e-8)
+    chib = np.array([0.02, 1.0, 16.0 / 3.0, 1e3])
+    yb = np.array([0.2, 0.7, -0.1, 3.0])
+    bw = mlp.output(1, yb, chib, u, 0.02, 1e3)
+    wb = 0.5 * np.sqrt(chib / (chib + 16.0 / 3.0))
+    assert wb[2] == pytest.approx(0.5 / math.sqrt(2.0))
+    assert np.allclose(bw, np.clip(0.5 - wb * yb, 0.0, 0.5)) and bw[2] == 0.5 and bw[3] == 0.0
+    # targets take the electron's fraction and fold it by U
+    xe = np.where(u <= 0.5, bw, 1 - bw)
+    tb = mlp.targets(1, chib, u, xe, 0.02, 1e3)
+    assert np.allclose(tb[:2], yb[:2])
     X = mlp.features(1, [1e-5, 1.0, 1e9], [0.2, 0.9, 0.5], 0.02, 1e3)
     assert X[0, 0] == -1.0 and X[2, 0] == 1.0
     assert np.allclose(X[:, 1], [2 * 0.4 - 1, 2 * 0.2 - 1, 1.0])
