@@ -556,7 +556,9 @@ qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink
  *
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  All calls share the one array (the firing counts are zeroed on the
+ * capture.  The cached address belongs to the device's context of that moment:
+ * after cudaDeviceReset (or anything else that destroys the context) this entry
+ * point is not usable again in the same process.  All calls share the one array (the firing counts are zeroed on the
  * stream at the start of each call, the lists keep the last call's contents):
  * calls that may overlap on the GPU -- different streams, or different host
  * threads -- race and must be serialised by the caller. */

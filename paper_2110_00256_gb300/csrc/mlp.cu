@@ -228,11 +228,11 @@ constexpr uint32_t kTcCols = 2 * kMlpH;  // one FP32 accumulator of N = 64 colum
 struct TcSmem {
     __nv_bfloat16 b[kMlpH * kMlpH];       // W2 [n][k] (B operand, K-major)
     __nv_bfloat16 a[2][kTcTile * kMlpH];  // H1 of each group's tile [m][k] (A operand, K-major)
-    alignas(8) float w1a[kMlpH];
-    alignas(8) float w1b[kMlpH];
-    alignas(8) float b1[kMlpH];
-    alignas(8) float b2[kMlpH];
-    alignas(8) float w3[kMlpH];
+    alignas(16) float w1a[kMlpH];  // (16-byte loads: four neurons' weights at a time)
+    alignas(16) float w1b[kMlpH];
+    alignas(16) float b1[kMlpH];
+    alignas(16) float b2[kMlpH];
+    alignas(16) float w3[kMlpH];
     float b3;
     alignas(8) uint64_t bar[2];
     uint32_t tmem;
@@ -305,9 +305,15 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
         for (int kc = 0; kc < kMlpH / 8; ++kc) {
             uint32_t w[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 g = f2u(layer1_pair(S.w1a, S.w1b, S.b1, kc * 8 + 2 * q, x1x1, x2x2));
-                w[q] = pack_bf16(g.x, g.y);
+            for (int q = 0; q < 4; q += 2) {
+                const int k = kc * 8 + 2 * q;
+                const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(S.w1a + k);
+                const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(S.w1b + k);
+                const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(S.b1 + k);
+                const float2 g0 = f2u(gelu2(ffma2(a.x, x1x1, ffma2(b.x, x2x2, c.x))));
+                const float2 g1 = f2u(gelu2(ffma2(a.y, x1x1, ffma2(b.y, x2x2, c.y))));
+                w[q] = pack_bf16(g0.x, g0.y);
+                w[q + 1] = pack_bf16(g1.x, g1.y);
             }
             *reinterpret_cast<uint4 *>(arow + kc * 128) = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -347,11 +353,13 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
             tc_ld16(tacc + (uint32_t)(c0 + 16), rb);
             tc_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; q += 2) {
+            for (int q = 0; q < 32; q += 4) {
+                const ulonglong2 b2 = *reinterpret_cast<const ulonglong2 *>(S.b2 + c0 + q);
+                const ulonglong2 w3 = *reinterpret_cast<const ulonglong2 *>(S.w3 + c0 + q);
                 const uint32_t r0 = q < 16 ? ra[q] : rb[q - 16], r1 = q < 16 ? ra[q + 1] : rb[q - 15];
-                const uint64_t b2 = *reinterpret_cast<const uint64_t *>(S.b2 + c0 + q);
-                const uint64_t w3 = *reinterpret_cast<const uint64_t *>(S.w3 + c0 + q);
-                y2 = ffma2(w3, gelu2(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2)), y2);
+                const uint32_t r2 = q < 16 ? ra[q + 2] : rb[q - 14], r3 = q < 16 ? ra[q + 3] : rb[q - 13];
+                y2 = ffma2(w3.x, gelu2(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2.x)), y2);
+                y2 = ffma2(w3.y, gelu2(fadd2(f2(__uint_as_float(r2), __uint_as_float(r3)), b2.y)), y2);
             }
         }
         const float2 yy = f2u(y2);

@@ -80,7 +80,8 @@ __device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b)
     return d;
 }
 
-// tanh of both lanes, evaluated on the FP16 pair
+// tanh of both lanes, evaluated on the FP16 pair (one special-function
+// operation for the two; ~2^-11 relative)
 __device__ __forceinline__ uint64_t tanh2(uint64_t u)
 {
     const float2 v = f2u(u);
@@ -93,6 +94,7 @@ __device__ __forceinline__ uint64_t tanh2(uint64_t u)
 
 // gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))  (Hendrycks & Gimpel)
 // on both lanes: h = x/2, u = x (sqrt(2/pi) + sqrt(2/pi) 0.044715 x^2), h + h tanh(u)
+// (FP32 pairs; the same speed as the whole GELU on FP16 pairs, measured, and more precise)
 __device__ __forceinline__ uint64_t gelu2(uint64_t x)
 {
     const uint64_t c1 = f2(0.035677408136300125f, 0.035677408136300125f);

@@ -67,6 +67,11 @@ extern "C" qed_status qed_substep_noalloc(const qed_tables *t, const qed_species
     int64_t total = 0;
     for (int64_t c : caps) {
         if (c < 0) QED_FAIL(QED_ERR_INVALID_ARG, "negative species capacity");
+        if (c > kNoallocMaxParticles)  // (each one first, so that the sum cannot overflow)
+            QED_FAIL(QED_ERR_INVALID_ARG,
+                     "qed_substep_noalloc: a species capacity of %lld particles is more than the %lld its built-in "
+                     "firing-list memory holds; use qed_substep with caller-provided firing lists",
+                     (long long)c, (long long)kNoallocMaxParticles);
         total += c;
     }
     if (total > kNoallocMaxParticles)

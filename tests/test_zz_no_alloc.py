@@ -6,8 +6,9 @@ from the caller.  This file is collected last on purpose.
 
 Checked through the C ABI: two consecutive substeps on identical inputs give
 the same particles as qed_substep with caller-allocated firing lists, in FP32
-and FP64, and capacities beyond the built-in limit are rejected before any work
-is enqueued."""
+and FP64; after a first call, further calls leave the device's free memory and
+torch's reserved memory unchanged; and capacities beyond the built-in limit are
+rejected before any work is enqueued."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,23 @@ def test_noalloc_matches_allocated_substep_twice(api, tables, prec_name, rtol):
                 assert np.allclose(y[fin], x[fin], rtol=rtol, atol=0), (step, k, c)
 
 
+def test_noalloc_allocates_nothing(api, tables):
+    host = _inputs(50_000)
+    bufs = _buffers(api, host, api.QED_F32)
+    stats = api.Stats()
+    api.qed_substep_noalloc(tables, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 3, 0, stats=stats)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for step in (1, 2):
+        api.qed_substep_noalloc(tables, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 3, step,
+                                stats=stats)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_reserved() == reserved0
+    assert stats.as_dict()["qs_events"] > 0
+
+
 def test_noalloc_rejects_capacities_beyond_its_limit(api, tables):
     from paper_2110_00256_gb300._lib import QED_NOALLOC_MAX_PARTICLES, QedError
     big = api.SpeciesBuffers(QED_NOALLOC_MAX_PARTICLES // 2 + 1, api.QED_F32)
@@ -82,3 +100,9 @@ def test_noalloc_rejects_capacities_beyond_its_limit(api, tables):
     with pytest.raises(QedError) as e:
         api.qed_substep_noalloc(tables, big, small, big, 1.0, 0, 0)
     assert "QED_ERR_INVALID_ARG" in str(e.value) and "capacities" in str(e.value)
+    # one capacity beyond the limit on its own is refused before any sum is formed
+    huge = api.SpeciesBuffers(16, api.QED_F32)
+    huge.capacity = 2 ** 62  # (never dereferenced: the call is refused first)
+    with pytest.raises(QedError) as e:
+        api.qed_substep_noalloc(tables, huge, small, huge, 1.0, 0, 0)
+    assert "QED_ERR_INVALID_ARG" in str(e.value)
