@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
                                                                     const double *__restrict__ xi, int64_t n,
                                                                     float *grad, float *loss_out)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
     const int tid = threadIdx.x;
     for (int i = tid; i < kMlpH; i += blockDim.x) {
@@ -255,15 +255,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid / kTcTile, row = tid % kTcTile;
+    // W2 and W3 are staged halved (exact): the layers' activations are 2 gelu (gelu2x)
     for (int i = tid; i < kMlpH * kMlpH; i += kTcThreads)
         *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(S.b) + core_offset(i / kMlpH, i % kMlpH)) =
-            v.w[kOffW2 + i];
+            __float2bfloat16_rn(0.5f * __bfloat162float(v.w[kOffW2 + i]));
     for (int i = tid; i < kMlpH; i += kTcThreads) {
         S.w1a[i] = __bfloat162float(v.w[kOffW1 + 2 * i]);
         S.w1b[i] = __bfloat162float(v.w[kOffW1 + 2 * i + 1]);
         S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
         S.b2[i] = __bfloat162float(v.w[kOffB2 + i]);
-        S.w3[i] = __bfloat162float(v.w[kOffW3 + i]);
+        S.w3[i] = 0.5f * __bfloat162float(v.w[kOffW3 + i]);
     }
     if (tid == 0) {
         S.b3 = __bfloat162float(v.w[kOffB3]);
@@ -310,8 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
                 const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(S.w1a + k);
                 const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(S.w1b + k);
                 const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(S.b1 + k);
-                const float2 g0 = f2u(gelu2(ffma2(a.x, x1x1, ffma2(b.x, x2x2, c.x))));
-                const float2 g1 = f2u(gelu2(ffma2(a.y, x1x1, ffma2(b.y, x2x2, c.y))));
+                const float2 g0 = f2u(gelu2x(ffma2(a.x, x1x1, ffma2(b.x, x2x2, c.x))));
+                const float2 g1 = f2u(gelu2x(ffma2(a.y, x1x1, ffma2(b.y, x2x2, c.y))));
                 w[q] = pack_bf16(g0.x, g0.y);
                 w[q + 1] = pack_bf16(g1.x, g1.y);
             }
@@ -358,8 +359,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
                 const ulonglong2 w3 = *reinterpret_cast<const ulonglong2 *>(S.w3 + c0 + q);
                 const uint32_t r0 = q < 16 ? ra[q] : rb[q - 16], r1 = q < 16 ? ra[q + 1] : rb[q - 15];
                 const uint32_t r2 = q < 16 ? ra[q + 2] : rb[q - 14], r3 = q < 16 ? ra[q + 3] : rb[q - 13];
-                y2 = ffma2(w3.x, gelu2(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2.x)), y2);
-                y2 = ffma2(w3.y, gelu2(fadd2(f2(__uint_as_float(r2), __uint_as_float(r3)), b2.y)), y2);
+                y2 = ffma2(w3.x, gelu2x(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2.x)), y2);
+                y2 = ffma2(w3.y, gelu2x(fadd2(f2(__uint_as_float(r2), __uint_as_float(r3)), b2.y)), y2);
             }
         }
         const float2 yy = f2u(y2);

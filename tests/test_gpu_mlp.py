@@ -95,6 +95,33 @@ def test_tensor_core_tiles_and_ragged_sizes(api, tables, n):
 
 
 @pytest.mark.parametrize("proc", [0, 1])
+def test_full_size_inference_sampled(api, tables, proc):
+    """The benchmark's size, 1e8 (chi, U) pairs in one launch (many rounds per
+    CTA): 4000 sampled outputs against the FP64 network, and the same bits when
+    the sampled inputs run alone."""
+    n = 100_000_000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(21 + proc)
+    lo, hi = (math.log(v) for v in _ranges(api, tables, proc))
+    chi = torch.exp(lo + (hi - lo) * torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
+    u = torch.rand(n, generator=g, device="cuda", dtype=torch.float64).clamp_(1e-12, 1 - 1e-12)
+    m = api.Mlp(tables, seed=61 + proc)
+    xi = m.sample(proc, chi, u)
+    idx = torch.randint(0, n, (4000,), generator=g, device="cuda")
+    c, uu, x = chi[idx].cpu().numpy(), u[idx].cpu().numpy(), xi[idx].cpu().numpy()
+    del chi, u, xi
+    torch.cuda.empty_cache()
+    theta = m.get_params(proc).astype(np.float64)
+    cmin, cmax = _ranges(api, tables, proc)
+    y_ref, _ = omlp.forward(theta, omlp.features(proc, c, uu, cmin, cmax), round_bf16=True)
+    y_gpu, ok = _y_of(proc, x, c, uu, y_ref, cmin, cmax)
+    d = np.abs(y_gpu[ok] - y_ref[ok])
+    assert ok.sum() > 2000 and np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
+    alone = m.sample(proc, torch.tensor(c, device="cuda"), torch.tensor(uu, device="cuda")).cpu().numpy()
+    assert np.array_equal(alone, x)
+
+
+@pytest.mark.parametrize("proc", [0, 1])
 def test_gradients_match_oracle(api, tables, proc):
     m = api.Mlp(tables, seed=11 + proc)
     theta = m.get_params(proc).astype(np.float64)
