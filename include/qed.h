@@ -521,7 +521,7 @@ qed_status qed_table_sample(const qed_tables *t, qed_process proc, qed_precision
  * QS grid is uniform in ln(xi / (1 - xi)), the BW grid in ln xi), per draw the
  * bracketing interval, a cubic Hermite first guess and Newton steps on the
  * partial integral.  d_work: device FP64 scratch of at least QED_EXACT_WORK(m)
- * entries.  Stream-ordered; m <= 2^31. */
+ * entries.  Stream-ordered; m < 2^31, m k <= 2^40. */
 #define QED_EXACT_WORK(m) ((int64_t)(m) * 2051)
 qed_status qed_exact_sample(qed_process proc, const double *d_chi, int64_t m, const double *d_u, int64_t k,
                             double *d_xi, double *d_work, int64_t work_capacity, void *stream);

@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
             continue;
         }
         tc_fence_after();
-        // bias, GELU and layer 3 on this thread's 64 accumulators, in pairs
+        // bias, GELU and layer 3 on this thread's 64 accumulators, in pairs (one
+        // partial sum: two measured the same)
         uint64_t y2 = f2(S.b3, 0.0f);
 #pragma unroll
         for (int c0 = 0; c0 < kMlpH; c0 += 32) {

@@ -420,7 +420,7 @@ extern "C" qed_status qed_exact_sample(qed_process proc, const double *d_chi, in
     if (m < 0 || k < 0) QED_FAIL(QED_ERR_INVALID_ARG, "negative sizes");
     if (m == 0 || k == 0) return QED_OK;
     if (!d_chi || !d_u || !d_xi || !d_work) QED_FAIL(QED_ERR_INVALID_ARG, "a device array is NULL");
-    if (m > (int64_t)1 << 31 || k > ((int64_t)1 << 40) / m) QED_FAIL(QED_ERR_INVALID_ARG, "too many draws");
+    if (m >= (int64_t)1 << 31 || k > ((int64_t)1 << 40) / m) QED_FAIL(QED_ERR_INVALID_ARG, "too many draws");
     if (work_capacity < QED_EXACT_WORK(m))
         QED_FAIL(QED_ERR_INVALID_ARG, "d_work holds %lld doubles, %lld needed", (long long)work_capacity,
                  (long long)QED_EXACT_WORK(m));
