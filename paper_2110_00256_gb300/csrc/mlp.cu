@@ -211,7 +211,7 @@ __global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfl
 // ---------------------------------------------------------------------------
 // batch inference with the 64x64 layer on the fifth-generation tensor cores.
 // A CTA of 256 threads is two independent groups of 128 (four warps each); a
-// group takes a tile of 128 samples per round: thread t of the group evaluates
+// group takes a tile of 128 samples per pass: thread t of the group evaluates
 // layer 1 of its sample into row t of the group's A operand (bf16, core-matrix
 // layout); one thread issues four K = 16 MMAs of M = 128, N = 64 into the
 // group's FP32 accumulator in tensor memory and commits them to the group's
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     uint32_t parity = 0;
     const int64_t stride = (int64_t)gridDim.x * 2 * kTcTile;
     const int64_t base0 = ((int64_t)blockIdx.x * 2 + grp) * kTcTile;
-    // (chi, U) of the next round are loaded one round ahead, so that their
-    // latency overlaps this round's work
+    // (chi, U) of the next tile are loaded one tile ahead, so that their
+    // latency overlaps this tile's work
     double c_next = base0 + row < n ? chi[base0 + row] : 1.0, u_next = base0 + row < n ? uu[base0 + row] : 0.5;
     for (int64_t base = base0; base < n; base += stride) {
         const int64_t i = base + row;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
             *reinterpret_cast<uint4 *>(arow + kc * 128) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_async_smem();
-        tc_fence_before();  // (orders the previous round's accumulator loads before the barrier)
+        tc_fence_before();  // (orders the previous tile's accumulator loads before the barrier)
         group_sync(grp);
         if (S.fail[grp]) {  // an earlier wait of this group gave up (never expected): stop
             for (int64_t b = base; b < n; b += stride)

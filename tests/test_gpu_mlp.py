@@ -50,10 +50,12 @@ def test_forward_matches_oracle(api, tables, proc):
     y_ref, _ = omlp.forward(theta, X, round_bf16=True)
     y_gpu, ok = _y_of(proc, xi, chi, u, y_ref, cmin, cmax)
     d = np.abs(y_gpu[ok] - y_ref[ok])
-    # the FP16 tanh (~2^-11), FP32 features and bf16 ties of h1 that flip between
-    # the FP32 and FP64 evaluations bound the difference
+    # tanh.approx (~2^-11 relative), the FP32 features and bf16 ties of h1 that flip
+    # between the FP32 and FP64 evaluations bound the difference (measured: median
+    # ~2e-7, 99.9th percentile <= 5e-5, largest 2.7e-4 in the output variable y)
     assert ok.sum() > 1000
-    assert np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
+    print(f"forward proc {proc}: median {np.median(d):.2e} p99.9 {np.percentile(d, 99.9):.2e} max {d.max():.2e}")
+    assert np.median(d) < 5e-6 and np.percentile(d, 99.9) < 1e-3 and d.max() < 5e-3, (np.median(d), d.max())
 
 
 def _y_of(proc, xi, chi, u, y_ref, cmin, cmax):
@@ -80,8 +82,8 @@ def _forward_error(api, tables, m, proc, chi, u):
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 256, 257, 300_001])
 def test_tensor_core_tiles_and_ragged_sizes(api, tables, n):
-    """The tcgen05 inference kernel takes 2 x 128 samples per CTA round (one
-    TMEM lane per sample): partial tiles, one sample, and many rounds per CTA
+    """The tcgen05 inference kernel takes 2 x 128 samples per CTA pass (one
+    TMEM lane per sample): partial tiles, one sample, and many tiles per CTA
     against the FP64 network; the same inputs give the same bits twice."""
     proc = n % 2
     m = api.Mlp(tables, seed=41 + proc)
@@ -89,14 +91,15 @@ def test_tensor_core_tiles_and_ragged_sizes(api, tables, n):
     xi, d = _forward_error(api, tables, m, proc, chi, u)
     assert np.all(np.isfinite(xi))
     if len(d):
-        assert np.max(d) < 2e-2 and np.median(d) < 2e-3, (np.median(d), np.max(d))
+        print(f"tiles n {n}: median {np.median(d):.2e} max {d.max():.2e}")
+        assert np.max(d) < 5e-3 and np.median(d) < 5e-6, (np.median(d), np.max(d))
     xi2 = m.sample(proc, torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
     assert np.array_equal(xi, xi2)
 
 
 @pytest.mark.parametrize("proc", [0, 1])
 def test_full_size_inference_sampled(api, tables, proc):
-    """The benchmark's size, 1e8 (chi, U) pairs in one launch (many rounds per
+    """The benchmark's size, 1e8 (chi, U) pairs in one launch (many tiles per
     CTA): 4000 sampled outputs against the FP64 network, and the same bits when
     the sampled inputs run alone."""
     n = 100_000_000
@@ -117,7 +120,9 @@ def test_full_size_inference_sampled(api, tables, proc):
     y_gpu, ok = _y_of(proc, x, c, uu, y_ref, cmin, cmax)
     d = np.abs(y_gpu[ok] - y_ref[ok])
     # (an untrained BW network clamps many outputs at 0 or 1/2: those carry no y)
-    assert ok.sum() > 1000 and np.median(d) < 2e-3 and np.percentile(d, 99.9) < 2e-2, (np.median(d), d.max())
+    print(f"full size proc {proc}: median {np.median(d):.2e} p99.9 {np.percentile(d, 99.9):.2e} max {d.max():.2e}")
+    assert ok.sum() > 1000 and np.median(d) < 5e-6 and np.percentile(d, 99.9) < 1e-3 and d.max() < 5e-3, \
+        (np.median(d), d.max())
     alone = m.sample(proc, torch.tensor(c, device="cuda"), torch.tensor(uu, device="cuda")).cpu().numpy()
     assert np.array_equal(alone, x)
 
