@@ -486,6 +486,16 @@ typedef struct qed_mlp qed_mlp; /* opaque, library-owned */
  * the input scaling takes the chi ranges of `t`.  Synchronises `stream`. */
 qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp **out, void *stream);
 qed_status qed_mlp_destroy(qed_mlp *m);
+/* Both networks to a file: their chi ranges and FP32 master parameters, with
+ * an FNV-1a checksum (the Adam moments are not kept).  Synchronous; the file
+ * is overwritten; QED_ERR_IO if it cannot be written. */
+qed_status qed_mlp_save(const qed_mlp *m, const char *path);
+/* A new qed_mlp (owned by the caller, freed with qed_mlp_destroy) from a file
+ * that qed_mlp_save wrote: the chi ranges come from the file, Adam starts
+ * afresh.  QED_ERR_IO (and *out = NULL) for a missing, short, corrupted
+ * (checksum) or foreign file, or one with non-finite parameters.
+ * Synchronises `stream`. */
+qed_status qed_mlp_load(const char *path, qed_mlp **out, void *stream);
 /* FP32 master parameters of one network to / from host memory (set also
  * refreshes the bf16 copy and clears the Adam moments; synchronous). */
 qed_status qed_mlp_get_params(const qed_mlp *m, qed_process proc, float *host_params);

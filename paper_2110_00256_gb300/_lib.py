@@ -130,6 +130,8 @@ SIGNATURES = {
     "qed_push_batched": (_S, [_P, C.POINTER(PlaneWave), _D, _D, _I64, _P, _P]),
     "qed_mlp_create": (_S, [_P, _U64, C.POINTER(_P), _P]),
     "qed_mlp_destroy": (_S, [_P]),
+    "qed_mlp_save": (_S, [_P, C.c_char_p]),
+    "qed_mlp_load": (_S, [C.c_char_p, C.POINTER(_P), _P]),
     "qed_mlp_get_params": (_S, [_P, _S, _P]),
     "qed_mlp_set_params": (_S, [_P, _S, _P, _P]),
     "qed_mlp_train_step": (_S, [_P, _S, _P, _P, _P, _I64, C.c_float, _P, _P]),

@@ -295,11 +295,25 @@ class Mlp:
 
     NPARAM = _lib.QED_MLP_PARAMS
 
-    def __init__(self, tables: Tables, seed: int = 0, stream=None):
+    def __init__(self, tables: Tables | None, seed: int = 0, stream=None, _handle=None):
         out = C.c_void_p()
-        check(lib().qed_mlp_create(tables.handle, int(seed), C.byref(out), _stream(stream)))
+        if _handle is None:
+            check(lib().qed_mlp_create(tables.handle, int(seed), C.byref(out), _stream(stream)))
+        else:
+            out = _handle
         self.handle = out
         self.tables = tables
+
+    def save(self, path: str):
+        """Both networks (chi ranges and FP32 parameters) to a file (qed_mlp_save)."""
+        check(lib().qed_mlp_save(self.handle, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Mlp":
+        """Networks that save() wrote (qed_mlp_load); the chi ranges come from the file."""
+        out = C.c_void_p()
+        check(lib().qed_mlp_load(str(path).encode(), C.byref(out), _stream(stream)))
+        return cls(None, _handle=out)
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -46,6 +46,18 @@ void clear_error();
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// 64-bit FNV-1a of a byte range (the checksum of the table and network files)
+inline uint64_t fnv1a64(const void *data, size_t n)
+{
+    const unsigned char *b = (const unsigned char *)data;
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
 // fine-structure constant, CODATA 2018 (the paper prints no value)
 constexpr double kAlpha = 7.2973525693e-3;
 

@@ -3,7 +3,9 @@
 // inference with the 64x64 layer on the tcgen05 tensor cores, and batch
 // sampling through the 2-D tables for comparison.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "launch.cuh"
 #include "mlp.cuh"
@@ -418,19 +420,14 @@ static void free_mlp(qed_mlp *m)
     delete m;
 }
 
-extern "C" qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp **out, void *stream)
+// both networks for the given chi ranges (index: process), weights from Philox(seed)
+static qed_status create_mlp(const double chi_min[2], const double chi_max[2], uint64_t seed, qed_mlp **out,
+                             cudaStream_t st)
 {
-    clear_error();
-    qed_status s;
-    if (!out) QED_FAIL(QED_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if ((s = check_tables(t))) return s;
     qed_mlp *m = new qed_mlp();
     memset(m, 0, sizeof(*m));
     cudaGetDevice(&m->device);
-    m->chi_min[0] = t->params.qs.chi_min, m->chi_max[0] = t->params.qs.chi_max;
-    m->chi_min[1] = t->params.bw.chi_min, m->chi_max[1] = t->params.bw.chi_max;
-    cudaStream_t st = as_stream(stream);
+    for (int p = 0; p < 2; ++p) m->chi_min[p] = chi_min[p], m->chi_max[p] = chi_max[p];
     for (int p = 0; p < 2; ++p) {
         cudaError_t e = cudaSuccess;
         float **fp[] = {&m->master[p], &m->adam_m[p], &m->adam_v[p], &m->grad[p]};
@@ -455,6 +452,96 @@ extern "C" qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp
         free_mlp(m);
         QED_FAIL(QED_ERR_CUDA, "mlp initialisation failed: %s", cudaGetErrorString(e));
     }
+    *out = m;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_create(const qed_tables *t, uint64_t seed, qed_mlp **out, void *stream)
+{
+    clear_error();
+    qed_status s;
+    if (!out) QED_FAIL(QED_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if ((s = check_tables(t))) return s;
+    const double lo[2] = {t->params.qs.chi_min, t->params.bw.chi_min};
+    const double hi[2] = {t->params.qs.chi_max, t->params.bw.chi_max};
+    return create_mlp(lo, hi, seed, out, as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// file format: "QEDMLP\0\1" | u32 version | u32 parameters per network |
+// chi_min[2] | chi_max[2] (FP64) | QS then BW FP32 master parameters
+// (little-endian host order) | u64 FNV-1a of everything before it
+// ---------------------------------------------------------------------------
+static const char kMlpMagic[8] = {'Q', 'E', 'D', 'M', 'L', 'P', 0, 1};
+static const uint32_t kMlpFileVersion = 1;
+static const size_t kMlpFileHead = 8 + 4 + 4 + 4 * 8;
+static const size_t kMlpFileBody = 2 * (size_t)kMlpParams * sizeof(float);
+
+extern "C" qed_status qed_mlp_save(const qed_mlp *m, const char *path)
+{
+    clear_error();
+    qed_status s = check_mlp(m, QED_PROC_QS);
+    if (s) return s;
+    if (!path) QED_FAIL(QED_ERR_INVALID_ARG, "path is NULL");
+    std::vector<unsigned char> buf(kMlpFileHead + kMlpFileBody);
+    unsigned char *q = buf.data();
+    const uint32_t n_params = kMlpParams;
+    memcpy(q, kMlpMagic, 8);
+    memcpy(q + 8, &kMlpFileVersion, 4);
+    memcpy(q + 12, &n_params, 4);
+    memcpy(q + 16, m->chi_min, 16);
+    memcpy(q + 32, m->chi_max, 16);
+    for (int p = 0; p < 2; ++p)
+        if ((s = qed_mlp_get_params(m, (qed_process)p, (float *)(q + kMlpFileHead) + (size_t)p * kMlpParams)))
+            return s;
+    const uint64_t h = fnv1a64(buf.data(), buf.size());
+    FILE *f = fopen(path, "wb");
+    if (!f) QED_FAIL(QED_ERR_IO, "cannot open %s for writing", path);
+    bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size() && fwrite(&h, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) QED_FAIL(QED_ERR_IO, "write to %s failed", path);
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_load(const char *path, qed_mlp **out, void *stream)
+{
+    clear_error();
+    if (!path || !out) QED_FAIL(QED_ERR_INVALID_ARG, "path/out is NULL");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) QED_FAIL(QED_ERR_IO, "cannot open %s", path);
+    std::vector<unsigned char> buf(kMlpFileHead + kMlpFileBody + 8 + 1);
+    const size_t got = fread(buf.data(), 1, buf.size(), f);
+    fclose(f);
+    if (got != kMlpFileHead + kMlpFileBody + 8) QED_FAIL(QED_ERR_IO, "%s: size %zu, not a network file", path, got);
+    if (memcmp(buf.data(), kMlpMagic, 8) != 0) QED_FAIL(QED_ERR_IO, "%s: bad magic", path);
+    uint32_t ver, n_params;
+    memcpy(&ver, buf.data() + 8, 4);
+    memcpy(&n_params, buf.data() + 12, 4);
+    if (ver != kMlpFileVersion) QED_FAIL(QED_ERR_IO, "%s: unsupported version %u", path, ver);
+    if (n_params != (uint32_t)kMlpParams) QED_FAIL(QED_ERR_IO, "%s: %u parameters per network, not %d", path, n_params, kMlpParams);
+    uint64_t h;
+    memcpy(&h, buf.data() + kMlpFileHead + kMlpFileBody, 8);
+    if (h != fnv1a64(buf.data(), kMlpFileHead + kMlpFileBody)) QED_FAIL(QED_ERR_IO, "%s: checksum mismatch", path);
+    double lo[2], hi[2];
+    memcpy(lo, buf.data() + 16, 16);
+    memcpy(hi, buf.data() + 32, 16);
+    for (int p = 0; p < 2; ++p)
+        if (!(lo[p] > 0 && hi[p] > lo[p] && std::isfinite(hi[p])))
+            QED_FAIL(QED_ERR_IO, "%s: bad chi range [%g, %g]", path, lo[p], hi[p]);
+    std::vector<float> params(2 * (size_t)kMlpParams);
+    memcpy(params.data(), buf.data() + kMlpFileHead, kMlpFileBody);
+    for (float v : params)
+        if (!std::isfinite(v)) QED_FAIL(QED_ERR_IO, "%s: non-finite parameter", path);
+    qed_mlp *m = nullptr;
+    qed_status s = create_mlp(lo, hi, 0, &m, as_stream(stream));
+    if (s) return s;
+    for (int p = 0; p < 2; ++p)
+        if ((s = qed_mlp_set_params(m, (qed_process)p, params.data() + (size_t)p * kMlpParams, stream))) {
+            free_mlp(m);
+            return s;
+        }
     *out = m;
     return QED_OK;
 }

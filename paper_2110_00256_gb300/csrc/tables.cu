@@ -281,16 +281,6 @@ extern "C" qed_status qed_tables_destroy(qed_tables *t)
 static const char kMagic[8] = {'Q', 'E', 'D', 'T', 'A', 'B', 0, 1};
 static const uint32_t kFileVersion = 1;
 
-static uint64_t fnv1a(const void *data, size_t n, uint64_t h)
-{
-    const unsigned char *b = (const unsigned char *)data;
-    for (size_t i = 0; i < n; ++i) {
-        h ^= b[i];
-        h *= 0x100000001b3ull;
-    }
-    return h;
-}
-
 static void put_axis(std::vector<unsigned char> &buf, const qed_table_axis &a)
 {
     auto put = [&](const void *p, size_t n) { buf.insert(buf.end(), (const unsigned char *)p, (const unsigned char *)p + n); };
@@ -317,7 +307,7 @@ extern "C" qed_status qed_tables_save(const qed_tables *t, const char *path)
     put_axis(buf, p.bw);
     for (auto *v : {&a, &b, &c, &d})
         buf.insert(buf.end(), (const unsigned char *)v->data(), (const unsigned char *)(v->data() + v->size()));
-    const uint64_t h = fnv1a(buf.data(), buf.size(), 0xcbf29ce484222325ull);
+    const uint64_t h = fnv1a64(buf.data(), buf.size());
     FILE *f = fopen(path, "wb");
     if (!f) QED_FAIL(QED_ERR_IO, "cannot open %s for writing", path);
     bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size() && fwrite(&h, 8, 1, f) == 1;
@@ -360,7 +350,7 @@ extern "C" qed_status qed_tables_load(const char *path, qed_tables **out, void *
     if (buf.size() != head + body + 8) QED_FAIL(QED_ERR_IO, "%s: size mismatch", path);
     uint64_t h;
     memcpy(&h, buf.data() + head + body, 8);
-    if (h != fnv1a(buf.data(), head + body, 0xcbf29ce484222325ull)) QED_FAIL(QED_ERR_IO, "%s: checksum mismatch", path);
+    if (h != fnv1a64(buf.data(), head + body)) QED_FAIL(QED_ERR_IO, "%s: checksum mismatch", path);
     const double *d = (const double *)(buf.data() + head);
     std::vector<double> arr(body / 8);
     memcpy(arr.data(), d, body);

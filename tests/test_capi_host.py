@@ -66,6 +66,53 @@ def test_argument_validation_without_gpu(lib):
     assert lib.qed_tables_destroy(None) == 0
 
 
+def _fnv1a64(b: bytes) -> int:
+    h = 0xcbf29ce484222325
+    for x in b:
+        h = ((h ^ x) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _mlp_file(params=None, magic=b"QEDMLP\0\1", version=1, n_params=None, ranges=(1e-3, 0.02, 1e3, 1e3)):
+    import struct
+    import numpy as np
+    from paper_2110_00256_gb300 import _lib
+    n = _lib.QED_MLP_PARAMS if n_params is None else n_params
+    p = np.zeros(2 * _lib.QED_MLP_PARAMS, np.float32) if params is None else params
+    body = magic + struct.pack("<II4d", version, n, *ranges) + p.tobytes()
+    return body + struct.pack("<Q", _fnv1a64(body))
+
+
+def test_network_file_rejected_before_the_device(lib, tmp_path):
+    """qed_mlp_load refuses missing, short, foreign, corrupted and non-finite
+    files with QED_ERR_IO before it allocates anything on the device."""
+    import numpy as np
+    from paper_2110_00256_gb300 import _lib
+    out = C.c_void_p(1)
+    assert lib.qed_mlp_load(b"/nonexistent/qed.mlp", C.byref(out), None) == 6 and not out.value
+    assert lib.qed_mlp_load(None, C.byref(out), None) == 1
+    assert lib.qed_mlp_save(None, b"x") == 1
+    good = _mlp_file()
+    cases = {
+        "short": good[:-9],
+        "long": good + b"\0",
+        "magic": _mlp_file(magic=b"QEDTAB\0\1"),
+        "version": _mlp_file(version=2),
+        "params": _mlp_file(n_params=4416),
+        "checksum": good[:100] + bytes([good[100] ^ 1]) + good[101:],
+        "range": _mlp_file(ranges=(1e-3, 0.02, 1e-4, 1e3)),
+        "nonfinite": _mlp_file(params=np.full(2 * _lib.QED_MLP_PARAMS, np.nan, np.float32)),
+    }
+    for name, data in cases.items():
+        path = tmp_path / f"{name}.mlp"
+        path.write_bytes(data)
+        out = C.c_void_p(1)
+        assert lib.qed_mlp_load(str(path).encode(), C.byref(out), None) == 6, name
+        assert not out.value, name
+        msg = lib.qed_last_error_message()
+        assert str(path).encode() in msg, (name, msg)
+
+
 def test_kernel_asymptote_constants_match_closed_forms():
     src = open(os.path.join(ROOT, "paper_2110_00256_gb300", "csrc", "physics.cuh")).read()
     ts = float(re.search(r"kTSmall\s*=\s*([0-9.eE+-]+)", src).group(1))

@@ -183,3 +183,27 @@ def test_substep_with_learned_sampler(api, tables):
                     [api.FireBuffers(3 * n) for _ in range(3)], stats=st2)
     torch.cuda.synchronize()
     assert st2.as_dict()["qs_events"] == s["qs_events"] and st2.as_dict()["pairs"] == s["pairs"]
+
+
+def test_save_and_load_give_the_same_sampler(api, tables, tmp_path):
+    """qed_mlp_save / qed_mlp_load: after a few training steps the networks go
+    to a file and come back with the same parameters and the same samples, bit
+    for bit (the chi ranges travel in the file), and keep training."""
+    m = api.Mlp(tables, seed=77)
+    for proc in (0, 1):
+        chi, u = _batch(api, tables, proc, 8192, 90 + proc)
+        c, uu = torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")
+        xi = api.qed_table_sample(tables, proc, api.QED_F64, c, uu)
+        for _ in range(3):
+            m.train_step(proc, c, uu, xi, 1e-3)
+    path = tmp_path / "sampler.mlp"
+    m.save(path)
+    m2 = api.Mlp.load(path)
+    for proc in (0, 1):
+        assert np.array_equal(m.get_params(proc), m2.get_params(proc))
+        chi, u = _batch(api, tables, proc, 30000, 95 + proc)
+        c, uu = torch.tensor(chi, device="cuda"), torch.tensor(u, device="cuda")
+        assert torch.equal(m.sample(proc, c, uu), m2.sample(proc, c, uu))
+        xi = api.qed_table_sample(tables, proc, api.QED_F64, c, uu)
+        m2.train_step(proc, c, uu, xi, 1e-3)
+        assert not np.array_equal(m.get_params(proc), m2.get_params(proc))
