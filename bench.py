@@ -84,7 +84,8 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "evolve_core.cuh", "physics.cuh", "common.cuh", "pipeline.cuh")
+KERNEL_SOURCES = ("evolve.cu", "evolve.cuh", "evolve_core.cuh", "physics.cuh", "common.cuh", "pipeline.cuh",
+                  "fp64_math.cuh", "fp64_tables.h")
 
 
 def kernel_hash() -> str:

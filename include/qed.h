@@ -547,6 +547,11 @@ qed_status qed_exact_sample(qed_process proc, const double *d_chi, int64_t m, co
  * double (never written in practice).  Synchronises `stream`. */
 qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
                               float *ms_out, void *stream);
+/* Not part of the method: the FP64 logarithm and exponential of the rate
+ * lookups (Tang's table-driven forms) beside the CUDA library's, for accuracy
+ * checks.  d_out: 4 n device doubles, written as [log_tang(x) | exp_tang(x) |
+ * log(x) | exp(x)] for the n device doubles d_x.  Stream-ordered; n <= 2^40. */
+qed_status qed_probe_fp64_logexp(const double *d_x, int64_t n, double *d_out, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* the substep without caller-provided working memory                        */

@@ -536,3 +536,13 @@ def qed_probe_fp64_fma(iters: int = 200_000, ctas_per_sm: int = 4, stream=None) 
     check(lib().qed_probe_fp64_fma(int(iters), int(ctas_per_sm), sink.data_ptr(), C.byref(r), C.byref(ms),
                                    _stream(stream)))
     return {"fma_per_s": r.value, "ms": ms.value}
+
+
+def qed_probe_fp64_logexp(x: torch.Tensor, stream=None) -> dict:
+    """The rate lookups' FP64 logarithm and exponential and the CUDA library's
+    on the device doubles x (include/qed.h)."""
+    x = x.contiguous()
+    out = torch.empty(4 * x.numel(), dtype=torch.float64, device=x.device)
+    check(lib().qed_probe_fp64_logexp(x.data_ptr(), int(x.numel()), out.data_ptr(), _stream(stream)))
+    o = out.view(4, -1)
+    return {"log": o[0], "exp": o[1], "log_lib": o[2], "exp_lib": o[3]}

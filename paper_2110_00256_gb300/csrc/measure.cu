@@ -1,6 +1,9 @@
 // measure.cu -- a standalone FP64 throughput probe: the peak against which the
 // FP64 evolution kernel (bound by GB300's FP64 pipe) is judged, measured by a
-// kernel that does nothing but dependent chains of fused multiply-adds.
+// kernel that does nothing but dependent chains of fused multiply-adds; and an
+// evaluation of the rate lookups' FP64 logarithm and exponential beside the
+// CUDA library's, for their accuracy checks.
+#include "fp64_math.cuh"
 #include "launch.cuh"
 
 namespace qed {
@@ -49,5 +52,33 @@ extern "C" qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, dou
     if (e != cudaSuccess) QED_FAIL(QED_ERR_CUDA, "probe failed: %s", cudaGetErrorString(e));
     *fma_per_s = (double)grid * 256.0 * kProbeChains * (double)iters / (ms * 1e-3);
     if (ms_out) *ms_out = ms;
+    return QED_OK;
+}
+
+namespace qed {
+
+__global__ void fp64_logexp_kernel(const double *x, int64_t n, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        out[i] = log_tang(v);
+        out[n + i] = exp_tang(v);
+        out[2 * n + i] = log(v);
+        out[3 * n + i] = exp(v);
+    }
+}
+
+}  // namespace qed
+
+extern "C" qed_status qed_probe_fp64_logexp(const double *d_x, int64_t n, double *d_out, void *stream)
+{
+    clear_error();
+    if (n < 0) QED_FAIL(QED_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return QED_OK;
+    if (!d_x || !d_out) QED_FAIL(QED_ERR_INVALID_ARG, "a pointer is NULL");
+    if (n > ((int64_t)1 << 40)) QED_FAIL(QED_ERR_INVALID_ARG, "n > 2^40");
+    const int64_t want = (n + 255) / 256, cap = 8 * (int64_t)sm_count();
+    fp64_logexp_kernel<<<(int)(want < cap ? want : cap), 256, 0, as_stream(stream)>>>(d_x, n, d_out);
+    QED_LAUNCH_CHECK();
     return QED_OK;
 }

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fp64_math.cuh"
 
 namespace qed {
 
@@ -17,11 +18,12 @@ __device__ __forceinline__ float d_fma(float a, float b, float c) { return fmaf(
 // logarithm and exponential of the 1-D rate lookups: in FP32 the hardware's
 // approximate forms (__logf: absolute error ~2^-21 near 1; __expf: ~2 + 1.2 |x|
 // ulp), whose ~1e-6 relative effect on a rate is far below the tables'
-// interpolation error; FP64 keeps the library functions
+// interpolation error; in FP64 Tang's table-driven forms (fp64_math.cuh, within
+// 2 ulp), which take fewer FP64 instructions than the library functions
 __device__ __forceinline__ float r_log(float x) { return __logf(x); }
-__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ double r_log(double x) { return log_tang(x); }
 __device__ __forceinline__ float r_exp(float x) { return __expf(x); }
-__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ double r_exp(double x) { return exp_tang(x); }
 __device__ __forceinline__ double d_fma(double a, double b, double c) { return fma(a, b, c); }
 
 // leading asymptotes of T outside the table (Eq. (t_func), read in the paper's
