@@ -211,43 +211,79 @@ __global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfl
 }
 
 // ---------------------------------------------------------------------------
-// batch inference with the 64x64 layer on the fifth-generation tensor cores.
-// A CTA of 256 threads is two independent groups of 128 (four warps each); a
-// group takes a tile of 128 samples per pass: thread t of the group evaluates
-// layer 1 of its sample into row t of the group's A operand (bf16, core-matrix
-// layout); one thread issues four K = 16 MMAs of M = 128, N = 64 into the
-// group's FP32 accumulator in tensor memory and commits them to the group's
-// mbarrier; then every thread reads the 64 accumulators of its own row (its TMEM
-// lane) back for bias, GELU and layer 3.  The groups synchronise only among
-// themselves (named barriers), so one group's layer 1 overlaps the other's MMA.
-// (The event kernels evaluate the network 32 samples per warp inside their own
-// loops and keep the warp-level mma.sync form of mlp_forward_warp.)
+// batch inference on the fifth-generation tensor cores.  A CTA of 256 threads
+// is two independent groups of 128 (four warps each); a group takes a tile of
+// 128 samples per pass, thread t owning sample t (row t of the group's A
+// operand, lane t of its tensor-memory accumulator).  Per tile:
+//   1. thread t writes its features into columns 64..79 of row t: x1 and x2
+//      each as three bf16 parts (h + m + l = x exactly: a float's 24 bits in
+//      three pieces of 8), a 1 and zeros;
+//   2. one thread issues layer 1 as one M = 128, N = 64, K = 16 MMA of those
+//      columns against [w1a w1a w1a w1b w1b w1b b1 0 ...] (the bias rides on
+//      the 1), commits it to the group's mbarrier;
+//   3. every thread reads its row's 64 FP32 sums back (tcgen05.ld), applies
+//      2 gelu and writes them, rounded to bf16, into columns 0..63 of its row;
+//   4. one thread issues layer 2 as five K = 16 MMAs: columns 0..63 against
+//      W2 / 2, then columns 64..79 against [0 0 0 0 0 0 b2 0 ...], which adds
+//      b2 through the same 1 (the accumulator of step 2 is overwritten);
+//   5. every thread reads its 64 sums back for bias-free GELU and layer 3
+//      (W3 / 2 and b3 on the CUDA cores).
+// Products of bf16 values are exact in the FP32 accumulator, so layer 1 is the
+// FP32 sum w1a x1 + w1b x2 + b1 up to the accumulation order.  The groups
+// synchronise only among themselves (named barriers), so one group's GELUs
+// overlap the other's MMAs.  (The event kernels evaluate the network 32
+// samples per warp inside their own loops and keep the warp-level mma.sync
+// form of mlp_forward_warp.)
 // ---------------------------------------------------------------------------
 constexpr int kTcThreads = 256;
 constexpr int kTcTile = 128;
+constexpr int kTcK = kMlpH + 16;         // the A operand's columns: activations, then features
 constexpr uint32_t kTcCols = 2 * kMlpH;  // one FP32 accumulator of N = 64 columns per group
 
 struct TcSmem {
-    __nv_bfloat16 b[kMlpH * kMlpH];       // W2 [n][k] (B operand, K-major)
-    __nv_bfloat16 a[2][kTcTile * kMlpH];  // H1 of each group's tile [m][k] (A operand, K-major)
-    alignas(16) float w1a[kMlpH];  // (16-byte loads: four neurons' weights at a time)
-    alignas(16) float w1b[kMlpH];
-    alignas(16) float b1[kMlpH];
-    alignas(16) float b2[kMlpH];
-    alignas(16) float w3[kMlpH];
+    __nv_bfloat16 a[2][kTcTile * kTcK];  // each group's A operand [m][k] (K-major, K = 80)
+    __nv_bfloat16 b2[kMlpH * kTcK];      // [W2 / 2 | b2 column] [n][k] (K-major, K = 80)
+    __nv_bfloat16 b1[kMlpH * 16];        // layer 1 against the split features [n][k] (K = 16)
+    alignas(16) float w3[kMlpH];         // W3 / 2
     float b3;
     alignas(8) uint64_t bar[2];
     uint32_t tmem;
     int fail[2];
 };
-// Dynamic shared memory per CTA, padded so that at most four CTAs share an SM:
-// four times kTcCols is the SM's 512 TMEM columns, so no allocation waits.
-constexpr int kTcSmemBytes = 48 * 1024;
-static_assert(sizeof(TcSmem) <= kTcSmemBytes, "shared memory of the tensor-core sampler");
+// Four CTAs share an SM at most (four times kTcCols is the SM's 512 TMEM columns,
+// and five times the shared memory does not fit), so no TMEM allocation waits.
+constexpr int kTcSmemBytes = (int)((sizeof(TcSmem) + 127) / 128 * 128);
+static_assert(4 * (kTcSmemBytes + 1024) <= 228 * 1024 && 5 * (kTcSmemBytes + 1024) > 228 * 1024,
+              "shared memory of the tensor-core sampler must admit exactly four CTAs per SM");
 
 __device__ __forceinline__ void group_sync(int group)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kTcTile) : "memory");
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+// x = h + m + l exactly, each a bf16 (round to nearest at every cut: the
+// remainders x - h and x - h - m are exact in FP32 and have at most 16 and 8
+// significant bits)
+__device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l)
+{
+    h = bf16_bits(x);
+    const float r1 = x - __uint_as_float((uint32_t)h << 16);
+    m = bf16_bits(r1);
+    const float r2 = r1 - __uint_as_float((uint32_t)m << 16);
+    l = bf16_bits(r2);
+}
+
+__device__ __forceinline__ uint32_t pack16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// columns 64..71 of a sample's A row: x1 and x2 in three bf16 parts each, 1, 0
+__device__ __forceinline__ uint4 feature_row(const MlpIn &in)
+{
+    uint16_t h1, m1, l1, h2, m2, l2;
+    split3(in.x1, h1, m1, l1);
+    split3(in.x2, h2, m2, l2);
+    return make_uint4(pack16(h1, m1), pack16(l1, h2), pack16(m2, l2), pack16(0x3f80u, 0));
 }
 
 __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
@@ -257,17 +293,27 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid / kTcTile, row = tid % kTcTile;
-    // W2 and W3 are staged halved (exact): the layers' activations are 2 gelu (gelu2x)
+    unsigned char *const b2raw = reinterpret_cast<unsigned char *>(S.b2);
+    // W2 is staged halved (exact): the activations are 2 gelu (gelu2x)
     for (int i = tid; i < kMlpH * kMlpH; i += kTcThreads)
-        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(S.b) + core_offset(i / kMlpH, i % kMlpH)) =
+        *reinterpret_cast<__nv_bfloat16 *>(b2raw + core_offset<kTcK>(i / kMlpH, i % kMlpH)) =
             __float2bfloat16_rn(0.5f * __bfloat162float(v.w[kOffW2 + i]));
-    for (int i = tid; i < kMlpH; i += kTcThreads) {
-        S.w1a[i] = __bfloat162float(v.w[kOffW1 + 2 * i]);
-        S.w1b[i] = __bfloat162float(v.w[kOffW1 + 2 * i + 1]);
-        S.b1[i] = __bfloat162float(v.w[kOffB1 + i]);
-        S.b2[i] = __bfloat162float(v.w[kOffB2 + i]);
-        S.w3[i] = 0.5f * __bfloat162float(v.w[kOffW3 + i]);
+    if (tid < kMlpH) {
+        const int r = tid;
+        const uint16_t wa = __bfloat16_as_ushort(v.w[kOffW1 + 2 * r]), wb = __bfloat16_as_ushort(v.w[kOffW1 + 2 * r + 1]);
+        const uint16_t c1 = __bfloat16_as_ushort(v.w[kOffB1 + r]), c2 = __bfloat16_as_ushort(v.w[kOffB2 + r]);
+        unsigned char *b1raw = reinterpret_cast<unsigned char *>(S.b1);
+        // layer 1 row r: the weights of x1's and x2's three parts, b1 on the 1
+        *reinterpret_cast<uint4 *>(b1raw + core_offset<16>(r, 0)) =
+            make_uint4(pack16(wa, wa), pack16(wa, wb), pack16(wb, wb), pack16(c1, 0));
+        *reinterpret_cast<uint4 *>(b1raw + core_offset<16>(r, 8)) = make_uint4(0, 0, 0, 0);
+        // layer 2 row r, columns 64..79: b2 on the 1, zero against the features
+        *reinterpret_cast<uint4 *>(b2raw + core_offset<kTcK>(r, kMlpH)) = make_uint4(0, 0, 0, pack16(c2, 0));
+        *reinterpret_cast<uint4 *>(b2raw + core_offset<kTcK>(r, kMlpH + 8)) = make_uint4(0, 0, 0, 0);
+        S.w3[r] = 0.5f * __bfloat162float(v.w[kOffW3 + r]);
     }
+    unsigned char *const arow = reinterpret_cast<unsigned char *>(S.a[grp]) + core_offset<kTcK>(row, 0);
+    *reinterpret_cast<uint4 *>(arow + core_offset<kTcK>(0, kMlpH + 8)) = make_uint4(0, 0, 0, 0);  // never rewritten
     if (tid == 0) {
         S.b3 = __bfloat162float(v.w[kOffB3]);
         S.fail[0] = S.fail[1] = 0;
@@ -276,102 +322,132 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTcCols);
-    fence_async_smem();  // W2 was written by ordinary stores and is read by the tensor core
+    fence_async_smem();  // the operands were written by ordinary stores and are read by the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
     constexpr uint32_t idesc = idesc_bf16_f32(kTcTile, kMlpH);
-    const uint64_t bdesc = smem_desc(smem_u32(S.b), 128, 1024);
-    const uint64_t adesc = smem_desc(smem_u32(S.a[grp]), 128, 1024);
-    const uint32_t dacc = tmem + (uint32_t)(grp * kMlpH);  // the group's accumulator (lane 0)
-    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[grp]) + core_offset(row, 0);
+    // (the operand descriptors are formed where the issuing thread needs them,
+    // which keeps them out of the other threads' registers)
+    constexpr uint64_t kFeat = (uint64_t)(kMlpH / 8 * 128 >> 4);  // descriptor step to columns 64..79
+    const uint32_t dacc = tmem + (uint32_t)(grp * kMlpH);          // the group's accumulator (lane 0)
     // this thread's row: TMEM lane 32 (warp % 4) + lane
     const uint32_t tacc = dacc + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t parity = 0;
     const int64_t stride = (int64_t)gridDim.x * 2 * kTcTile;
     const int64_t base0 = ((int64_t)blockIdx.x * 2 + grp) * kTcTile;
-    // (chi, U) of the next tile are loaded one tile ahead, so that their
-    // latency overlaps this tile's work
-    double c_next = base0 + row < n ? chi[base0 + row] : 1.0, u_next = base0 + row < n ? uu[base0 + row] : 0.5;
+    // Software pipeline within the group: the features of tile k + 1 are formed
+    // while the layer-2 MMAs of tile k run, the output map of tile k while the
+    // layer-1 MMA of tile k + 1 runs, and (chi, U) are loaded two tiles ahead.
+    MlpIn in = mlp_input(v, base0 + row < n ? chi[base0 + row] : 1.0, base0 + row < n ? uu[base0 + row] : 0.5);
+    uint4 feat = feature_row(in);
+    double c_next = base0 + stride + row < n ? chi[base0 + stride + row] : 1.0;
+    double u_next = base0 + stride + row < n ? uu[base0 + stride + row] : 0.5;
+    MlpIn in_prev = in;
+    int64_t i_prev = n;  // (no previous tile yet)
+    float y_prev = 0.0f;
+    // A wait that gives up (never expected) sets the group's flag; from the
+    // next barrier on, the group issues no MMA, waits for none and writes NaN,
+    // but keeps passing the same barriers, so that no thread waits for one that
+    // left the loop.
     for (int64_t base = base0; base < n; base += stride) {
         const int64_t i = base + row;
-        const bool valid = i < n;
-        const double c = c_next, u = u_next;
-        const int64_t j = i + stride;
-        c_next = j < n ? chi[j] : 1.0;
-        u_next = j < n ? uu[j] : 0.5;
-        const MlpIn in = mlp_input(v, c, u);
-        // layer 1 on the CUDA cores, rounded to bf16 into row `row` of the A tile
-        const uint64_t x1x1 = f2(in.x1, in.x1), x2x2 = f2(in.x2, in.x2);
-#pragma unroll
-        for (int kc = 0; kc < kMlpH / 8; ++kc) {
-            uint32_t w[4];
-#pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-                const int k = kc * 8 + 2 * q;
-                const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(S.w1a + k);
-                const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(S.w1b + k);
-                const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(S.b1 + k);
-                const float2 g0 = f2u(gelu2x(ffma2(a.x, x1x1, ffma2(b.x, x2x2, c.x))));
-                const float2 g1 = f2u(gelu2x(ffma2(a.y, x1x1, ffma2(b.y, x2x2, c.y))));
-                w[q] = pack_bf16(g0.x, g0.y);
-                w[q + 1] = pack_bf16(g1.x, g1.y);
-            }
-            *reinterpret_cast<uint4 *>(arow + kc * 128) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
+        *reinterpret_cast<uint4 *>(arow + core_offset<kTcK>(0, kMlpH)) = feat;
         fence_async_smem();
         tc_fence_before();  // (orders the previous tile's accumulator loads before the barrier)
         group_sync(grp);
-        if (S.fail[grp]) {  // an earlier wait of this group gave up (never expected): stop
-            for (int64_t b = base; b < n; b += stride)
-                if (b + row < n) xi[b + row] = __longlong_as_double(0x7ff8000000000000LL);
-            break;
-        }
-        if (row == 0) {
+        bool live = S.fail[grp] == 0;
+        if (live && row == 0) {
             tc_fence_after();
-            // layer 2: Z = H1 W2^T, K = 64 in four steps of 16 (two core matrices, 256 bytes)
+            const uint64_t adesc = smem_desc(smem_u32(S.a[grp]), 128, kTcK * 16);
+            tc_mma_bf16(dacc, adesc + kFeat, smem_desc(smem_u32(S.b1), 128, 16 * 16), idesc, false);  // layer 1
+            tc_commit(&S.bar[grp]);
+        }
+        if (i_prev < n) xi[i_prev] = mlp_output(v.proc, y_prev, in_prev);  // the previous tile (NaN y: NaN)
+        bool ok = live && mbar_wait(&S.bar[grp], parity);
+        if (live) parity ^= 1u;
+        if (live && !ok) {
+            S.fail[grp] = 1;  // seen by the whole group after its next barrier
+            note_error(QED_EW_WAIT_TIMEOUT);
+        }
+        if (ok) {
+            tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < kMlpH / 16; ++kk) {
+            for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+                uint32_t ra[16];
+                tc_ld16(tacc + (uint32_t)c0, ra);
+                tc_wait_ld();
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {  // eight columns, one 16-byte store
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int e = 8 * kc + 2 * q;
+                        const uint32_t r0 = ra[e], r1 = ra[e + 1];
+                        const float2 g = f2u(gelu2x(f2(__uint_as_float(r0), __uint_as_float(r1))));
+                        w[q] = pack_bf16(g.x, g.y);
+                    }
+                    *reinterpret_cast<uint4 *>(arow + core_offset<kTcK>(0, c0 + 8 * kc)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();  // (the layer-1 loads complete before layer 2 overwrites the accumulator)
+        group_sync(grp);
+        live = S.fail[grp] == 0;
+        if (live && row == 0) {
+            tc_fence_after();
+            // layer 2: Z = H1 W2^T / 2 + b2, K = 80 in five steps of 16 (two core matrices, 256 bytes)
+            const uint64_t adesc = smem_desc(smem_u32(S.a[grp]), 128, kTcK * 16);
+            const uint64_t b2desc = smem_desc(smem_u32(S.b2), 128, kTcK * 16);
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
                 const uint64_t step = (uint64_t)(kk * 256 >> 4);
-                tc_mma_bf16(dacc, adesc + step, bdesc + step, idesc, kk > 0);
+                tc_mma_bf16(dacc, adesc + step, b2desc + step, idesc, kk > 0);
             }
             tc_commit(&S.bar[grp]);
         }
-        const bool done = mbar_wait(&S.bar[grp], parity);
-        parity ^= 1u;
-        if (!done) {
-            S.fail[grp] = 1;  // seen by the whole group after its next barrier
+        in_prev = in;
+        i_prev = i;
+        in = mlp_input(v, c_next, u_next);
+        feat = feature_row(in);
+        const int64_t j = i + 2 * stride;
+        c_next = j < n ? chi[j] : 1.0;
+        u_next = j < n ? uu[j] : 0.5;
+        ok = live && mbar_wait(&S.bar[grp], parity);
+        if (live) parity ^= 1u;
+        if (live && !ok) {
+            S.fail[grp] = 1;
             note_error(QED_EW_WAIT_TIMEOUT);
-            if (valid) xi[i] = __longlong_as_double(0x7ff8000000000000LL);
-            continue;
         }
-        tc_fence_after();
-        // bias, GELU and layer 3 on this thread's 64 accumulators, in pairs (one
-        // partial sum: two measured the same)
-        uint64_t y2 = f2(S.b3, 0.0f);
+        float y = __int_as_float(0x7fc00000);
+        if (ok) {
+            tc_fence_after();
+            // GELU and layer 3 on this thread's 64 accumulators, in pairs
+            uint64_t y2 = f2(S.b3, 0.0f);
 #pragma unroll
-        for (int c0 = 0; c0 < kMlpH; c0 += 32) {
-            uint32_t ra[16], rb[16];
-            tc_ld16(tacc + (uint32_t)c0, ra);  // two loads in flight, one wait
-            tc_ld16(tacc + (uint32_t)(c0 + 16), rb);
-            tc_wait_ld();
+            for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+                uint32_t ra[16];
+                tc_ld16(tacc + (uint32_t)c0, ra);
+                tc_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; q += 4) {
-                const ulonglong2 b2 = *reinterpret_cast<const ulonglong2 *>(S.b2 + c0 + q);
-                const ulonglong2 w3 = *reinterpret_cast<const ulonglong2 *>(S.w3 + c0 + q);
-                const uint32_t r0 = q < 16 ? ra[q] : rb[q - 16], r1 = q < 16 ? ra[q + 1] : rb[q - 15];
-                const uint32_t r2 = q < 16 ? ra[q + 2] : rb[q - 14], r3 = q < 16 ? ra[q + 3] : rb[q - 13];
-                y2 = ffma2(w3.x, gelu2x(fadd2(f2(__uint_as_float(r0), __uint_as_float(r1)), b2.x)), y2);
-                y2 = ffma2(w3.y, gelu2x(fadd2(f2(__uint_as_float(r2), __uint_as_float(r3)), b2.y)), y2);
+                for (int q = 0; q < 16; q += 4) {
+                    const ulonglong2 w3 = *reinterpret_cast<const ulonglong2 *>(S.w3 + c0 + q);
+                    y2 = ffma2(w3.x, gelu2x(f2(__uint_as_float(ra[q]), __uint_as_float(ra[q + 1]))), y2);
+                    y2 = ffma2(w3.y, gelu2x(f2(__uint_as_float(ra[q + 2]), __uint_as_float(ra[q + 3]))), y2);
+                }
             }
+            const float2 yy = f2u(y2);
+            y = yy.x + yy.y;
         }
-        const float2 yy = f2u(y2);
-        if (valid) xi[i] = mlp_output(v.proc, yy.x + yy.y, in);
+        y_prev = y;
     }
+    if (i_prev < n) xi[i_prev] = mlp_output(v.proc, y_prev, in_prev);
     tc_fence_before();
     __syncthreads();
-    if (S.fail[grp]) mbar_wait(&S.bar[grp], parity ^ 1u);  // one more bounded wait for the MMAs in flight
+    if (S.fail[grp]) mbar_wait(&S.bar[grp], parity ^ 1u);  // one more bounded wait for an MMA in flight
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -653,7 +729,7 @@ extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const d
     if (n == 0) return QED_OK;
     static bool attr = false;
     if (!attr) {
-        // the largest shared-memory carveout, so that four CTAs (48 KB each) fit on an SM
+        // the largest shared-memory carveout, so that four CTAs (53 KB each) fit on an SM
         QED_CUDA_TRY(
             cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes));
         QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,

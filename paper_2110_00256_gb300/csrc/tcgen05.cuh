@@ -4,10 +4,10 @@
 // the FP32 accumulator back into registers.
 //
 // Operand layout used here (no swizzle, both operands K-major): a matrix of R
-// rows and K = 64 bf16 columns is stored as 8 x 8 "core matrices" of 128 bytes
-// (8 rows of 16 bytes); core matrices adjacent along K are 128 bytes apart
-// (leading-dimension offset), 8-row groups are 1024 bytes apart (stride
-// offset).
+// rows and K bf16 columns is stored as "core matrices" of 128 bytes (8 rows of
+// 16 bytes, 8 columns); core matrices adjacent along K are 128 bytes apart
+// (leading-dimension offset), 8-row groups are K x 16 bytes apart (stride
+// offset: 1280 bytes for K = 80, 256 for K = 16).
 #pragma once
 
 #include <cstdint>
@@ -16,10 +16,11 @@
 
 namespace qed {
 
-// byte offset of element (r, k) of a K = 64 bf16 operand in the layout above
+// byte offset of element (r, k) of a K-column bf16 operand in the layout above
+template <int K>
 __device__ __forceinline__ uint32_t core_offset(int r, int k)
 {
-    return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
 // shared-memory matrix descriptor: start address, leading- and stride-dimension
