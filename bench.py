@@ -37,6 +37,8 @@ SEED = 20211001
 BYTES_F32 = 52  # algorithmic bytes per evolved particle: p, E, B, tau, tau_c read (44) + tau, tau_c written (8)
 BYTES_F64 = 88  # p, E, B, tau read (80) + tau written (8)
 FALLBACK_HBM_GBS = 6800.0
+TANH_PER_SAMPLE = 128  # the learned sampler's GELUs: two hidden layers of 64
+TC_FLOP_PER_SAMPLE = 2 * 64 * (16 + 80)  # its tensor-core MMAs: layer 1 (K = 16) and layer 2 (K = 80)
 
 
 def headline_config(n: int, ws: int) -> dict:
@@ -339,6 +341,21 @@ def mlp_leg(api, tabs, bufs, fire, args, ws):
                                       "table256_f32": tail(api.qed_table_sample(tabs, 0, api.QED_F32, ct, ut))}
     out["params_bytes_bf16_per_network"] = 2 * 4417
     out["table_bytes_fp32_256x256_per_process"] = 2 * 256 * 256 * 4
+    # The sampler kernel's roofline: its GELUs take 128 tanh.approx.f32 per sample
+    # on the special-function units (the largest stall is that queue), measured
+    # against a kernel of nothing but tanh chains; the tensor cores' share beside it.
+    probe = max((api.qed_probe_tanh(ctas_per_sm=c) for c in (4, 8)), key=lambda r: r["tanh_per_s"])
+    rate = min(out["qs_mlp_samples_per_s"], out["bw_mlp_samples_per_s"])
+    ach = TANH_PER_SAMPLE * rate
+    peaks_ = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks_.get("bf16_tflops", 1900.0)) * 1e12
+    out["roofline"] = {"bound": "alu", "kernel": "mlp_sample_tc_kernel", "unit": "tanh/s", "achieved": ach,
+                       "peak": probe["tanh_per_s"], "frac": round(ach / probe["tanh_per_s"], 4),
+                       "peak_kind": "measured: qed_probe_tanh (dependent tanh.approx.f32 chains) on this GPU",
+                       "tanh_per_sample": TANH_PER_SAMPLE, "samples_per_s": rate,
+                       "tensor_flop_per_sample": TC_FLOP_PER_SAMPLE,
+                       "tensor_frac_of_bf16_peak": round(TC_FLOP_PER_SAMPLE * rate / bf16, 4)}
     return out
 
 

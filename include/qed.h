@@ -547,6 +547,16 @@ qed_status qed_exact_sample(qed_process proc, const double *d_chi, int64_t m, co
  * double (never written in practice).  Synchronises `stream`. */
 qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
                               float *ms_out, void *stream);
+/* Not part of the method: the rate of tanh.approx.f32 on this GPU's
+ * special-function units, the operation that bounds the learned sampler's GELUs
+ * (two layers of 64 per sample).  The same form as qed_probe_fp64_fma: a kernel
+ * of nothing but dependent chains x <- tanh(x) / 2 + 1/2 (8 per thread, 256
+ * threads per CTA, ctas_per_sm CTAs per SM, `iters` steps per chain), timed
+ * with CUDA events around one launch after a warm-up launch; *tanh_per_s
+ * receives tanh evaluations per second.  d_sink: one device double (never
+ * written in practice).  Synchronises `stream`. */
+qed_status qed_probe_tanh(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *tanh_per_s, float *ms_out,
+                          void *stream);
 /* Not part of the method: the FP64 logarithm and exponential of the rate
  * lookups (Tang's table-driven forms) beside the CUDA library's, for accuracy
  * checks.  d_out: 4 n device doubles, written as [log_tang(x) | exp_tang(x) |

@@ -143,6 +143,7 @@ SIGNATURES = {
     "qed_compact_species": (_S, [C.POINTER(Species), _S, _P, _I64, _P, _P]),
     "qed_exact_sample": (_S, [_S, _P, _I64, _P, _I64, _P, _P, _I64, _P]),
     "qed_probe_fp64_fma": (_S, [_I64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_float), _P]),
+    "qed_probe_tanh": (_S, [_I64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_float), _P]),
     "qed_probe_fp64_logexp": (_S, [_P, _I64, _P, _P]),
 }
 QED_MLP_PARAMS = 4417

@@ -25,7 +25,7 @@ __all__ = [
     "qed_substep_noalloc", "qed_version", "Mlp", "qed_table_sample", "substep_opts_mlp", "SubstepCall",
     "Batch", "qed_substep_batched", "qed_tune_evolve", "make_opts", "plane_wave", "qed_push_plane_wave", "qed_push_stored_fields", "qed_push_substep_batched",
     "qed_schwinger_pairs",
-    "qed_push_batched", "qed_exact_sample", "qed_probe_fp64_fma", "qed_device_status", "qed_species_energy", "qed_compact_species", "CompactWork",
+    "qed_push_batched", "qed_exact_sample", "qed_probe_fp64_fma", "qed_probe_tanh", "qed_device_status", "qed_species_energy", "qed_compact_species", "CompactWork",
 ]
 
 FIELDS = ("px", "py", "pz", "ex", "ey", "ez", "bx", "by", "bz")
@@ -536,6 +536,15 @@ def qed_probe_fp64_fma(iters: int = 200_000, ctas_per_sm: int = 4, stream=None) 
     check(lib().qed_probe_fp64_fma(int(iters), int(ctas_per_sm), sink.data_ptr(), C.byref(r), C.byref(ms),
                                    _stream(stream)))
     return {"fma_per_s": r.value, "ms": ms.value}
+
+
+def qed_probe_tanh(iters: int = 200_000, ctas_per_sm: int = 8, stream=None) -> dict:
+    """tanh.approx.f32 evaluations per second of this GPU (include/qed.h)."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    r, ms = C.c_double(), C.c_float()
+    check(lib().qed_probe_tanh(int(iters), int(ctas_per_sm), sink.data_ptr(), C.byref(r), C.byref(ms),
+                               _stream(stream)))
+    return {"tanh_per_s": r.value, "ms": ms.value}
 
 
 def qed_probe_fp64_logexp(x: torch.Tensor, stream=None) -> dict:

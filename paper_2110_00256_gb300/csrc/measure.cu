@@ -1,10 +1,12 @@
-// measure.cu -- a standalone FP64 throughput probe: the peak against which the
+// measure.cu -- standalone throughput probes: the FP64 peak against which the
 // FP64 evolution kernel (bound by GB300's FP64 pipe) is judged, measured by a
-// kernel that does nothing but dependent chains of fused multiply-adds; and an
-// evaluation of the rate lookups' FP64 logarithm and exponential beside the
-// CUDA library's, for their accuracy checks.
+// kernel that does nothing but dependent chains of fused multiply-adds; the
+// special-function unit's tanh.approx.f32 rate, which bounds the learned
+// sampler's GELUs; and an evaluation of the rate lookups' FP64 logarithm and
+// exponential beside the CUDA library's, for their accuracy checks.
 #include "fp64_math.cuh"
 #include "launch.cuh"
+#include "mlp.cuh"
 
 namespace qed {
 
@@ -25,24 +27,34 @@ __global__ void __launch_bounds__(256) fp64_fma_kernel(int64_t iters, double a, 
     if (s == 1234.5678) sink[0] = s;  // keeps the chains alive; never true for these inputs
 }
 
-}  // namespace qed
-
-using namespace qed;
-
-extern "C" qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
-                                         float *ms_out, void *stream)
+// dependent chains x <- a tanh(x) + b: one tanh.approx.f32 and one FMA per step
+__global__ void __launch_bounds__(256) tanh_kernel(int64_t iters, float a, float b, double *sink)
 {
-    clear_error();
-    if (iters <= 0 || ctas_per_sm <= 0 || ctas_per_sm > 32 || !d_sink || !fma_per_s)
-        QED_FAIL(QED_ERR_INVALID_ARG, "bad probe arguments");
-    cudaStream_t st = as_stream(stream);
-    const int grid = sm_count() * ctas_per_sm;
+    float x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = (float)(threadIdx.x + c) * 1e-3f;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = fmaf(a, tanh_approx(x[c]), b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c];
+    if (s == 1234.5678f) sink[0] = s;  // keeps the chains alive; never true for these inputs
+}
+
+// one warm-up launch, then one timed launch of `kernel` on `grid` CTAs of 256;
+// *ops_per_s = grid x 256 x kProbeChains x iters / time
+template <typename A>
+static qed_status time_probe(void (*kernel)(int64_t, A, A, double *), int64_t iters, A a, A b, int grid,
+                             double *d_sink, double *ops_per_s, float *ms_out, cudaStream_t st)
+{
     cudaEvent_t e0, e1;
     QED_CUDA_TRY(cudaEventCreate(&e0));
     QED_CUDA_TRY(cudaEventCreate(&e1));
-    fp64_fma_kernel<<<grid, 256, 0, st>>>(iters / 10 + 1, 0.999999, 1e-7, d_sink);  // warm-up
+    kernel<<<grid, 256, 0, st>>>(iters / 10 + 1, a, b, d_sink);  // warm-up
     cudaEventRecord(e0, st);
-    fp64_fma_kernel<<<grid, 256, 0, st>>>(iters, 0.999999, 1e-7, d_sink);
+    kernel<<<grid, 256, 0, st>>>(iters, a, b, d_sink);
     cudaEventRecord(e1, st);
     const cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -50,9 +62,33 @@ extern "C" qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, dou
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) QED_FAIL(QED_ERR_CUDA, "probe failed: %s", cudaGetErrorString(e));
-    *fma_per_s = (double)grid * 256.0 * kProbeChains * (double)iters / (ms * 1e-3);
+    *ops_per_s = (double)grid * 256.0 * kProbeChains * (double)iters / (ms * 1e-3);
     if (ms_out) *ms_out = ms;
     return QED_OK;
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" qed_status qed_probe_tanh(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *tanh_per_s,
+                                     float *ms_out, void *stream)
+{
+    clear_error();
+    if (iters <= 0 || ctas_per_sm <= 0 || ctas_per_sm > 32 || !d_sink || !tanh_per_s)
+        QED_FAIL(QED_ERR_INVALID_ARG, "bad probe arguments");
+    return time_probe(tanh_kernel, iters, 0.5f, 0.5f, sm_count() * ctas_per_sm, d_sink, tanh_per_s, ms_out,
+                      as_stream(stream));
+}
+
+extern "C" qed_status qed_probe_fp64_fma(int64_t iters, int32_t ctas_per_sm, double *d_sink, double *fma_per_s,
+                                         float *ms_out, void *stream)
+{
+    clear_error();
+    if (iters <= 0 || ctas_per_sm <= 0 || ctas_per_sm > 32 || !d_sink || !fma_per_s)
+        QED_FAIL(QED_ERR_INVALID_ARG, "bad probe arguments");
+    return time_probe(fp64_fma_kernel, iters, 0.999999, 1e-7, sm_count() * ctas_per_sm, d_sink, fma_per_s, ms_out,
+                      as_stream(stream));
 }
 
 namespace qed {

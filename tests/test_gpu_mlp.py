@@ -207,3 +207,16 @@ def test_save_and_load_give_the_same_sampler(api, tables, tmp_path):
         xi = api.qed_table_sample(tables, proc, api.QED_F64, c, uu)
         m2.train_step(proc, c, uu, xi, 1e-3)
         assert not np.array_equal(m.get_params(proc), m2.get_params(proc))
+
+
+def test_tanh_probe(api):
+    """qed_probe_tanh, the peak the sampler kernel's roofline is reported
+    against: a positive rate, at most the 128 FP32 lanes per SM per clock that
+    the special-function units cannot exceed, at least one per SM per clock, and
+    bad arguments refused before anything runs."""
+    r = api.qed_probe_tanh(iters=20_000, ctas_per_sm=8)
+    prop = torch.cuda.get_device_properties(0)
+    per_sm_clk = r["tanh_per_s"] / (prop.multi_processor_count * 2.07e9)
+    assert r["ms"] > 0 and 1.0 < per_sm_clk < 128.0, r
+    with pytest.raises(RuntimeError):
+        api.qed_probe_tanh(iters=0)
