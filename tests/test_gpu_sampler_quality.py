@@ -7,7 +7,10 @@ quadrature of the spectra, no table):
 * the networks, trained on 10^7 exact samples by the library's own kernels,
   against the oracle's CDF in 5 chi bins of each table range, beside the
   256 x 256 FP32 tables on the same draws: the KS distance of every bin
-  stays below a stated bound (QS 0.01, BW 0.02);
+  stays below a stated bound (0.005 for both), the largest sup |P - U| of a
+  single chi below 0.003 (QS) and 0.01 (BW), and in the two highest-chi bins
+  the QS network's is under half the table's (the table's last log-spaced
+  xi interval, below);
 * the hard-photon tail at chi = 9, where the 256-point log-spaced xi grid puts
   its last interval at [0.897, 1] and the table's log-log interpolation spreads
   the hardest emissions across it: P(xi > 0.99) is 1.1e-6 exactly, ~1.4e-3
@@ -33,7 +36,8 @@ pytestmark = pytest.mark.gpu
 BINS = 5
 CHI_PER_BIN = 4
 NU = 500
-KS_BOUND = {0: 0.01, 1: 0.02}
+KS_BOUND = {0: 0.005, 1: 0.005}
+WORST_CHI_BOUND = {0: 0.003, 1: 0.01}
 
 
 @pytest.fixture(scope="module")
@@ -138,6 +142,9 @@ def test_network_ks_per_chi_bin(api, tables, trained, pool, proc):
     print(f"         256x256 FP32 table   {[round(a, 5) for a, _ in rt]} (worst chi {[round(b, 5) for _, b in rt]})")
     print(f"         training: {reps[proc]['seconds']:.1f} s, final loss {reps[proc]['final_loss']:.3e}")
     assert max(a for a, _ in rn) <= KS_BOUND[proc]
+    assert max(b for _, b in rn) <= WORST_CHI_BOUND[proc]
+    if proc == 0:  # where the table's hard end is coarse, the network is the better sampler
+        assert all(rn[i][1] < 0.5 * rt[i][1] for i in (BINS - 2, BINS - 1))
 
 
 def test_network_tail_and_memory_against_table(api, tables, trained):
