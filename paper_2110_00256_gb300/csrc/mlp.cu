@@ -211,10 +211,15 @@ __global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfl
 }
 
 // ---------------------------------------------------------------------------
-// batch inference on the fifth-generation tensor cores.  A CTA of 256 threads
-// is two independent groups of 128 (four warps each); a group takes a tile of
-// 128 samples per pass, thread t owning sample t (row t of the group's A
-// operand, lane t of its tensor-memory accumulator).  Per tile:
+// batch inference on the fifth-generation tensor cores.  One CTA of 1024
+// threads per SM, eight independent groups of 128 (four warps each); a group
+// takes a tile of 128 samples per pass, thread t owning sample t (row t of the
+// group's A operand, lane t of its tensor-memory accumulator).  Each CTA owns
+// an equal contiguous range of tiles, and its groups claim the tiles of that
+// range one at a time from a shared-memory counter: the warp schedulers favour
+// some warps over others, and with a fixed share per group the favoured groups
+// finished early and left their SM short of warps for the rest of the launch
+// (a quarter of the warp slots idle on average).  Per tile:
 //   1. thread t writes its features into columns 64..79 of row t: x1 and x2
 //      each as three bf16 parts (h + m + l = x exactly: a float's 24 bits in
 //      three pieces of 8), a 1 and zeros;
@@ -235,26 +240,29 @@ __global__ void mlp_adam_kernel(float *p, float *m, float *v, float *g, __nv_bfl
 // samples per warp inside their own loops and keep the warp-level mma.sync
 // form of mlp_forward_warp.)
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 256;
+constexpr int kTcGroups = 8;
 constexpr int kTcTile = 128;
-constexpr int kTcK = kMlpH + 16;         // the A operand's columns: activations, then features
-constexpr uint32_t kTcCols = 2 * kMlpH;  // one FP32 accumulator of N = 64 columns per group
+constexpr int kTcThreads = kTcGroups * kTcTile;  // 1024
+constexpr int kTcK = kMlpH + 16;                 // the A operand's columns: activations, then features
+constexpr uint32_t kTcCols = kTcGroups * kMlpH;  // one FP32 accumulator of N = 64 columns per group: all 512
 
 struct TcSmem {
-    __nv_bfloat16 a[2][kTcTile * kTcK];  // each group's A operand [m][k] (K-major, K = 80)
-    __nv_bfloat16 b2[kMlpH * kTcK];      // [W2 / 2 | b2 column] [n][k] (K-major, K = 80)
-    __nv_bfloat16 b1[kMlpH * 16];        // layer 1 against the split features [n][k] (K = 16)
-    alignas(16) float w3[kMlpH];         // W3 / 2
+    __nv_bfloat16 a[kTcGroups][kTcTile * kTcK];  // each group's A operand [m][k] (K-major, K = 80)
+    __nv_bfloat16 b2[kMlpH * kTcK];              // [W2 / 2 | b2 column] [n][k] (K-major, K = 80)
+    __nv_bfloat16 b1[kMlpH * 16];                // layer 1 against the split features [n][k] (K = 16)
+    alignas(16) float w3[kMlpH];                 // W3 / 2
     float b3;
-    alignas(8) uint64_t bar[2];
+    alignas(8) uint64_t bar[kTcGroups];
     uint32_t tmem;
-    int fail[2];
+    int fail[kTcGroups];
+    int next;                                    // tiles of the CTA's range handed out so far
+    int claim[kTcGroups];                        // each group's tile two passes ahead
 };
-// Four CTAs share an SM at most (four times kTcCols is the SM's 512 TMEM columns,
-// and five times the shared memory does not fit), so no TMEM allocation waits.
+// One CTA per SM (its registers and shared memory leave room for no second
+// one), holding all 512 TMEM columns, so no TMEM allocation waits.
 constexpr int kTcSmemBytes = (int)((sizeof(TcSmem) + 127) / 128 * 128);
-static_assert(4 * (kTcSmemBytes + 1024) <= 228 * 1024 && 5 * (kTcSmemBytes + 1024) > 228 * 1024,
-              "shared memory of the tensor-core sampler must admit exactly four CTAs per SM");
+static_assert(kTcSmemBytes + 1024 <= 228 * 1024 && 2 * (kTcSmemBytes + 1024) > 228 * 1024,
+              "shared memory of the tensor-core sampler must admit exactly one CTA per SM");
 
 __device__ __forceinline__ void group_sync(int group)
 {
@@ -286,7 +294,7 @@ __device__ __forceinline__ uint4 feature_row(const MlpIn &in)
     return make_uint4(pack16(h1, m1), pack16(l1, h2), pack16(m2, l2), pack16(0x3f80u, 0));
 }
 
-__global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_sample_tc_kernel(MlpView v, const double *__restrict__ chi,
                                                                      const double *__restrict__ uu, int64_t n,
                                                                      double *__restrict__ xi)
 {
@@ -316,9 +324,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     *reinterpret_cast<uint4 *>(arow + core_offset<kTcK>(0, kMlpH + 8)) = make_uint4(0, 0, 0, 0);  // never rewritten
     if (tid == 0) {
         S.b3 = __bfloat162float(v.w[kOffB3]);
-        S.fail[0] = S.fail[1] = 0;
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
+        for (int g = 0; g < kTcGroups; ++g) {
+            S.fail[g] = 0;
+            mbar_init(&S.bar[g], 1);
+        }
+        S.next = 2 * kTcGroups;  // the first two tiles of every group are fixed (below)
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTcCols);
@@ -335,15 +345,23 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     // this thread's row: TMEM lane 32 (warp % 4) + lane
     const uint32_t tacc = dacc + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t parity = 0;
-    const int64_t stride = (int64_t)gridDim.x * 2 * kTcTile;
-    const int64_t base0 = ((int64_t)blockIdx.x * 2 + grp) * kTcTile;
+    // the CTA's tiles t_begin + [0, t_len); group g starts on its tiles g and
+    // g + kTcGroups, then claims one tile per pass from S.next (tile numbers
+    // relative to t_begin: a CTA's range stays far below 2^31 tiles)
+    const int64_t n_tiles = (n + kTcTile - 1) / kTcTile;
+    const int64_t t_begin = (int64_t)blockIdx.x * n_tiles / gridDim.x;
+    const int t_len = (int)(((int64_t)blockIdx.x + 1) * n_tiles / gridDim.x - t_begin);
+    const int64_t s_begin = t_begin * kTcTile + row;  // this thread's sample in tile 0
+    int t_cur = grp, t_nxt = grp + kTcGroups;
     // Software pipeline within the group: the features of tile k + 1 are formed
     // while the layer-2 MMAs of tile k run, the output map of tile k while the
     // layer-1 MMA of tile k + 1 runs, and (chi, U) are loaded two tiles ahead.
-    MlpIn in = mlp_input(v, base0 + row < n ? chi[base0 + row] : 1.0, base0 + row < n ? uu[base0 + row] : 0.5);
+    const int64_t i0 = s_begin + (int64_t)t_cur * kTcTile, i1 = s_begin + (int64_t)t_nxt * kTcTile;
+    const bool v0 = t_cur < t_len && i0 < n, v1 = t_nxt < t_len && i1 < n;
+    MlpIn in = mlp_input(v, v0 ? chi[i0] : 1.0, v0 ? uu[i0] : 0.5);
     uint4 feat = feature_row(in);
-    double c_next = base0 + stride + row < n ? chi[base0 + stride + row] : 1.0;
-    double u_next = base0 + stride + row < n ? uu[base0 + stride + row] : 0.5;
+    double c_next = v1 ? chi[i1] : 1.0;
+    double u_next = v1 ? uu[i1] : 0.5;
     MlpIn in_prev = in;
     int64_t i_prev = n;  // (no previous tile yet)
     float y_prev = 0.0f;
@@ -351,12 +369,14 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
     // next barrier on, the group issues no MMA, waits for none and writes NaN,
     // but keeps passing the same barriers, so that no thread waits for one that
     // left the loop.
-    for (int64_t base = base0; base < n; base += stride) {
-        const int64_t i = base + row;
+    while (t_cur < t_len) {
+        const int64_t i = s_begin + (int64_t)t_cur * kTcTile;
         *reinterpret_cast<uint4 *>(arow + core_offset<kTcK>(0, kMlpH)) = feat;
+        if (row == 0) S.claim[grp] = atomicAdd(&S.next, 1);  // (read by the group after the barrier)
         fence_async_smem();
         tc_fence_before();  // (orders the previous tile's accumulator loads before the barrier)
         group_sync(grp);
+        const int t_nn = S.claim[grp];  // (rewritten only after the group's next barrier)
         bool live = S.fail[grp] == 0;
         if (live && row == 0) {
             tc_fence_after();
@@ -413,9 +433,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) mlp_sample_tc_kernel(MlpView v,
         i_prev = i;
         in = mlp_input(v, c_next, u_next);
         feat = feature_row(in);
-        const int64_t j = i + 2 * stride;
-        c_next = j < n ? chi[j] : 1.0;
-        u_next = j < n ? uu[j] : 0.5;
+        const int64_t j = s_begin + (int64_t)t_nn * kTcTile;
+        const bool vj = t_nn < t_len && j < n;
+        c_next = vj ? chi[j] : 1.0;
+        u_next = vj ? uu[j] : 0.5;
+        t_cur = t_nxt;
+        t_nxt = t_nn;
         ok = live && mbar_wait(&S.bar[grp], parity);
         if (live) parity ^= 1u;
         if (live && !ok) {
@@ -729,15 +752,16 @@ extern "C" qed_status qed_mlp_sample(const qed_mlp *m, qed_process proc, const d
     if (n == 0) return QED_OK;
     static bool attr = false;
     if (!attr) {
-        // the largest shared-memory carveout, so that four CTAs (53 KB each) fit on an SM
+        // the largest shared-memory carveout (the CTA takes 177 KB)
         QED_CUDA_TRY(
             cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes));
         QED_CUDA_TRY(cudaFuncSetAttribute(mlp_sample_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           (int)cudaSharedmemCarveoutMaxShared));
         attr = true;
     }
-    // four CTAs per SM (the TMEM budget; more never become resident), fewer for small batches
-    const int64_t want = (n + 2 * kTcTile - 1) / (2 * kTcTile), cap = (int64_t)sm_count() * 4;
+    // one CTA per SM (it holds all of the SM's TMEM), fewer for small batches
+    const int64_t want = (n + (int64_t)kTcGroups * kTcTile - 1) / ((int64_t)kTcGroups * kTcTile),
+                  cap = (int64_t)sm_count();
     const int blocks = (int)(want < cap ? want : cap);
     mlp_sample_tc_kernel<<<blocks, kTcThreads, kTcSmemBytes, as_stream(stream)>>>(mlp_view(m, proc), d_chi, d_u, n,
                                                                                  d_xi);

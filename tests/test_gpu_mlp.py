@@ -80,11 +80,14 @@ def _forward_error(api, tables, m, proc, chi, u):
     return xi, np.abs(y_gpu[ok] - y_ref[ok])
 
 
-@pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 256, 257, 300_001])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 256, 257, 300_001, 3_000_001])
 def test_tensor_core_tiles_and_ragged_sizes(api, tables, n):
-    """The tcgen05 inference kernel takes 2 x 128 samples per CTA pass (one
-    TMEM lane per sample): partial tiles, one sample, and many tiles per CTA
-    against the FP64 network; the same inputs give the same bits twice."""
+    """The tcgen05 inference kernel: eight groups per CTA, 128 samples per
+    group and pass (one TMEM lane per sample), each CTA an equal range of
+    tiles, of which every group takes two fixed ones and then claims the rest
+    one at a time (3e6 samples: ~150 tiles per CTA, most of them claimed).
+    Partial tiles, one sample, and many tiles per CTA against the FP64
+    network; the same inputs give the same bits twice."""
     proc = n % 2
     m = api.Mlp(tables, seed=41 + proc)
     chi, u = _batch(api, tables, proc, n, 50 + n)
