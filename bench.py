@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-cascade", action="store_true")
     ap.add_argument("--no-schwinger", action="store_true")
     ap.add_argument("--no-longrun", action="store_true")
+    ap.add_argument("--no-paper-table", action="store_true")
     ap.add_argument("--cascade-scale", type=float, default=1.0,
                     help="fraction of the 64 patch counts round(10^(3+4U)) to run in the cascade leg")
     ap.add_argument("--cascade-steps", type=int, default=2000)
@@ -356,6 +357,96 @@ def mlp_leg(api, tabs, bufs, fire, args, ws):
                        "tanh_per_sample": TANH_PER_SAMPLE, "samples_per_s": rate,
                        "tensor_flop_per_sample": TC_FLOP_PER_SAMPLE,
                        "tensor_frac_of_bf16_peak": round(TC_FLOP_PER_SAMPLE * rate / bf16, 4)}
+    return out
+
+
+# The paper's kernel timings (Table tab:comp, quoted for context): ms to apply one
+# kernel to all 10^8 particles of the §4 distribution, FP64 / FP32, on a Quadro GV100 (CUDA)
+PAPER_GV100_MS = {"bw_evol": (14.52, 7.43), "bw_prod": (29.94, 15.70), "qs_evol": (14.62, 7.39),
+                  "qs_em": (26.88, 14.15)}
+
+
+def paper_table_leg(api, tabs, n=100_000_000, reps=5, precs=None):
+    """Table tab:comp of the paper on this GPU: each of its four kernels applied to
+    all n particles of the §4 distribution (one species), FP64 and FP32.  Evolution:
+    qed_evolve_optical_depth with dt = 10 (a few particles fire).  Production /
+    emission: every particle fires (its optical depth set below zero and evolved
+    once, which lists all of them with their chi), then qed_generate_pairs /
+    qed_generate_photons runs on all n; before each repetition the state the
+    event kernel changed is restored and the destinations emptied (outside the
+    CUDA events, which bracket the call alone)."""
+    import torch
+
+    from paper_2110_00256_gb300 import workloads
+    out = {"workload": "%g particles of the paper's benchmark distribution (one species per kernel), every "
+                       "kernel applied to all of them; production/emission: every particle fires" % n,
+           "gb300_ms": {}, "paper_gv100_cuda_ms": {k: {"f64": v[0], "f32": v[1]} for k, v in PAPER_GV100_MS.items()}}
+
+    def timed(fn, before=None):
+        ms = []
+        for r in range(reps + 1):
+            if before:
+                before()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if r:  # the first call is a warm-up
+                ms.append(a.elapsed_time(b))
+        return round(sorted(ms)[len(ms) // 2], 4)
+
+    for prec, key in ((api.QED_F64, "f64"), (api.QED_F32, "f32")):
+        if precs is not None and prec not in precs:
+            continue
+        dt_ = torch.float64 if prec == api.QED_F64 else torch.float32
+        for proc, name in ((api.QED_PROC_QS, "qs"), (api.QED_PROC_BW, "bw")):
+            sp = api.SpeciesBuffers(n, prec)
+            d = workloads.paper_benchmark_torch(n, 31 + proc, 0, dtype=dt_)
+            for c, v in d.items():
+                sp.arrays[c][:n].copy_(v)
+            del d
+            sp.count.fill_(n)
+            fire = api.FireBuffers(n)
+            out["gb300_ms"].setdefault(name + "_evol", {})[key] = timed(
+                lambda: api.qed_evolve_optical_depth(tabs, proc, sp, DT, fire))
+            # every particle fires: the event kernel then runs on all n
+            sp.arrays["tau"][:n].fill_(-1.0)
+            sp.arrays["tau_c"][:n].zero_()
+            api.qed_evolve_optical_depth(tabs, proc, sp, DT, fire)
+            torch.cuda.synchronize()
+            assert fire.n() == n
+            changed = ("px", "py", "pz", "tau", "tau_c") if proc == api.QED_PROC_QS else ("tau", "tau_c", "weight")
+            saved = {c: sp.arrays[c][:n].clone() for c in changed}
+            if proc == api.QED_PROC_QS:
+                dst = api.SpeciesBuffers(n, prec)
+
+                def restore():
+                    for c in changed:
+                        sp.arrays[c][:n].copy_(saved[c])
+                    dst.count.zero_()
+                out["gb300_ms"].setdefault("qs_em", {})[key] = timed(
+                    lambda: api.qed_generate_photons(tabs, sp, dst, fire, SEED, 7), restore)
+                made = dst.n()
+            else:
+                ele, pos = api.SpeciesBuffers(n, prec), api.SpeciesBuffers(n, prec)
+
+                def restore():
+                    for c in changed:
+                        sp.arrays[c][:n].copy_(saved[c])
+                    ele.count.zero_()
+                    pos.count.zero_()
+                out["gb300_ms"].setdefault("bw_prod", {})[key] = timed(
+                    lambda: api.qed_generate_pairs(tabs, sp, ele, pos, fire, SEED, 7), restore)
+                made = ele.n()
+                del ele, pos
+            out.setdefault("secondaries_per_call", {})[name + "_" + key] = made
+            del sp, fire, saved
+            if proc == api.QED_PROC_QS:
+                del dst
+            torch.cuda.empty_cache()
+    out["speedup_vs_gv100"] = {k: {p: round(out["paper_gv100_cuda_ms"][k][p] / v * n / 1e8, 1)
+                                   for p, v in d_.items()} for k, d_ in out["gb300_ms"].items()}
     return out
 
 
@@ -899,6 +990,9 @@ def gpu_main(args):
 
     if not args.no_mlp:
         result.setdefault("paths", {})["fp32_mlp"] = mlp_leg(api, tabs, bufs, fire, args, ws)
+
+    if not args.no_paper_table:
+        result["paper_table"] = paper_table_leg(api, tabs)
 
     if not args.no_cascade:
         del bufs, fire

@@ -100,7 +100,9 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint64_t id, int64_t step, uin
 __device__ __forceinline__ double uniform53(uint32_t lo, uint32_t hi)
 {
     const uint64_t v = (((uint64_t)hi << 32) | lo) >> 11;
-    return ((double)v + 0.5) * 0x1.0p-53;
+    // ((double)v + 0.5) 2^-53 with one rounding: the fused form rounds the same
+    // exact value once, and the scaling by 2^-53 is exact either way
+    return fma((double)v, 0x1.0p-53, 0x1.0p-54);
 }
 
 // ---------------------------------------------------------------------------

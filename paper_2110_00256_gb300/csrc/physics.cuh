@@ -25,6 +25,13 @@ __device__ __forceinline__ double r_log(double x) { return log_tang(x); }
 __device__ __forceinline__ float r_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double r_exp(double x) { return exp_tang(x); }
 __device__ __forceinline__ double d_fma(double a, double b, double c) { return fma(a, b, c); }
+// logarithm and exponential of the 2-D inverse-CDF sampling: FP32 the library
+// forms; FP64 Tang's (ln chi and ln r are interpolation coordinates, where the
+// logarithm's 2^-57 absolute error near 1 is far below the tables' spacing)
+__device__ __forceinline__ float s_log(float x) { return logf(x); }
+__device__ __forceinline__ double s_log(double x) { return log_tang(x); }
+__device__ __forceinline__ float s_exp(float x) { return expf(x); }
+__device__ __forceinline__ double s_exp(double x) { return exp_tang(x); }
 
 // leading asymptotes of T outside the table (Eq. (t_func), read in the paper's
 // chi_gamma convention): T ~ 3 sqrt(3) / (16 sqrt(2)) exp(-8 / (3 chi)) for
@@ -179,7 +186,7 @@ __device__ __forceinline__ void locate_2d(const Table2D<T> &tb, T chi, const T *
                                           size_t &off, int &row)
 {
     T c = chi < tb.chi_min ? tb.chi_min : (chi > tb.chi_max ? tb.chi_max : chi);
-    T t = (d_log(c) - tb.ln_min) * tb.inv_d;
+    T t = (s_log(c) - tb.ln_min) * tb.inv_d;
     t = t < T(0) ? T(0) : (t > T(tb.n_chi - 1) ? T(tb.n_chi - 1) : t);
     int n = (int)t;
     n = n > tb.n_chi - 2 ? tb.n_chi - 2 : n;
@@ -228,7 +235,7 @@ __device__ __forceinline__ T qs_sample_xi(const Table2D<T> &tb, T chi, T r)
     size_t off;
     int row;
     locate_2d(tb, chi, r0, r1, w, off, row);
-    const T lr = d_log(r);
+    const T lr = s_log(r);
     const int *g0 = tb.guide + (size_t)row * (kGuideBins + 1);
     int b = (int)(r * T(kGuideBins));
     b = b > kGuideBins - 1 ? kGuideBins - 1 : (b < 0 ? 0 : b);
@@ -237,10 +244,10 @@ __device__ __forceinline__ T qs_sample_xi(const Table2D<T> &tb, T chi, T r)
     const T dp = row_val(tb.dv + off, tb.dv + off + tb.n_xi, w, m);  // P_{m+1} - P_m
     const T x0 = tb.x0 + T(m) * tb.dx;
     const T x1 = (m + 1 == tb.n_xi - 1) ? T(0) : tb.x0 + T(m + 1) * tb.dx;
-    if (!(dp > T(0))) return d_exp(x0);
+    if (!(dp > T(0))) return s_exp(x0);
     T lx = x0 + (lr - p0) * (x1 - x0) / dp;
     lx = lx > T(0) ? T(0) : lx;
-    return d_exp(lx);
+    return s_exp(lx);
 }
 
 // BW inverse CDF (§3.1): r <= 1/2 samples the electron, otherwise the positron
@@ -285,11 +292,33 @@ __device__ __forceinline__ void store_tau<float>(float *tau, float *tau_c, int64
     tau_c[i] = __double2float_rn((double)h - x);
 }
 
+// -ln U in FP64 for U in [2^-54, 1]: Tang's logarithm (within 2 ulp); above
+// 1 - 2^-8, where ln U is small and that logarithm's error no longer shrinks
+// with it, the Taylor series of log1p(d) with d = U - 1 (exact: U >= 1/2), whose
+// remainder d^8/8 is below 2^-59 of the result.  The optical-depth resets are
+// the event kernels' largest FP64 cost, and GB300's FP64 pipe their bound when
+// many particles fire.
+__device__ __forceinline__ double neg_log_u(double u)
+{
+    // (positive doubles order as their bit patterns: the test costs no FP64
+    // instruction, and U >= 2^-54 is normal, so Tang's core needs no range check)
+    if (__double_as_longlong(u) > __double_as_longlong(1.0 - 0x1p-8)) {
+        const double d = u - 1.0;
+        double q = fma(d, -1.0 / 7, 1.0 / 6);
+        q = fma(d, q, -0.2);
+        q = fma(d, q, 0.25);
+        q = fma(d, q, -1.0 / 3);
+        q = fma(d, q, 0.5);
+        return fma(d * d, q, -d);  // -(d - d^2/2 + d^3/3 - ... - d^7/7)
+    }
+    return -log_tang_core(u, 0);
+}
+
 // tau = -ln U, U the 53-bit uniform of (seed, (id, step, purpose)), in FP64 (§3)
 __device__ __forceinline__ double tau_draw(uint64_t seed, uint64_t id, int64_t step, uint32_t purpose)
 {
     const U4 w = draw(seed, id, step, purpose);
-    return -log(uniform53(w.x, w.y));
+    return neg_log_u(uniform53(w.x, w.y));
 }
 
 }  // namespace qed
