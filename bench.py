@@ -9,6 +9,12 @@ tables of 256 points and 256x256 generated in FP64 on the GPU, dt = 10 hbar/(m_e
 One step = one qed_substep call: evolution of all three species in one batched
 launch, pair production, photon emission, secondaries appended.
 
+Further legs (each with its own key in the same line): the evolution kernel's
+variants, the end-to-end leg from host buffers, the FP64 table path, the learned
+sampler, the paper's per-kernel table (each of its four kernels on all 1e8
+particles, FP64 and FP32), the cascade, the batched substep, Schwinger pairs,
+the 1000-step QS + BW workload, and the oracle timed on the host cores.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
 """
