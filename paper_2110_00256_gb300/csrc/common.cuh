@@ -100,9 +100,16 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint64_t id, int64_t step, uin
 __device__ __forceinline__ double uniform53(uint32_t lo, uint32_t hi)
 {
     const uint64_t v = (((uint64_t)hi << 32) | lo) >> 11;
-    // ((double)v + 0.5) 2^-53 with one rounding: the fused form rounds the same
-    // exact value once, and the scaling by 2^-53 is exact either way
-    return fma((double)v, 0x1.0p-53, 0x1.0p-54);
+    // ((double)v + 0.5) 2^-53 assembled from integer operations, bit for bit the
+    // same double without an FP64 instruction: v + 1/2 is exact below 2^52 and
+    // rounds to even above it, so U = M 2^-k with M = 2v + 1, k = 54 (v < 2^52)
+    // or M = v + (v & 1), k = 53; M < 2^53 except M = 2^53 (U = 1)
+    const bool big = v >= (1ull << 52);
+    const uint64_t m = big ? v + (v & 1ull) : 2ull * v + 1ull;
+    const int k = big ? 53 : 54;
+    const int len = 64 - __clzll((long long)m);  // bit length, 1 .. 54
+    const uint64_t frac = (len <= 53 ? m << (53 - len) : m >> 1) & 0xfffffffffffffull;
+    return __longlong_as_double((long long)(((uint64_t)(len - 1 - k + 1023) << 52) | frac));
 }
 
 // ---------------------------------------------------------------------------

@@ -284,12 +284,47 @@ template <typename T>
 __device__ __forceinline__ void store_tau(T *tau, T *tau_c, int64_t i, double x);
 template <>
 __device__ __forceinline__ void store_tau<double>(double *tau, double *, int64_t i, double x) { tau[i] = x; }
+// (h, c) = (fl32(x), fl32(h - x)), both rounded to nearest even.  Where both are
+// normal floats (2^-74 <= |x| < 2^127) from the bits of x with integer
+// operations, without an FP64 instruction (GB300's FP64 pipe bounds the event
+// kernels when many particles fire): h keeps the top 24 of x's 53 significant
+// bits, rounded; h - x is the rounding residual, an integer of at most 29 bits
+// times 2^(e - 52), exact in FP64, rounded once by the integer-to-float
+// conversion and scaled exactly.  Elsewhere (0, tiny, huge, infinite, NaN) by
+// FP64 conversions, with the same results.
+__device__ __forceinline__ void split_f32_pair(double x, float &h, float &c)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -74 || e > 126) {
+        h = __double2float_rn(x);
+        c = __double2float_rn((double)h - x);
+        return;
+    }
+    const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53 significant bits
+    unsigned int keep = (unsigned int)(m >> 29);                                  // the top 24
+    const unsigned int rem = (unsigned int)(m & 0x1fffffffu);                     // the other 29
+    const bool up = rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u));
+    int diff = up ? (int)(0x20000000u - rem) : -(int)rem;  // (|h| - |x|) / 2^(e - 52)
+    keep += up ? 1u : 0u;
+    int eh = e;
+    if (keep == 0x1000000u) {  // rounded up into the next binade
+        keep >>= 1;
+        ++eh;
+    }
+    const bool neg = (b >> 63) != 0;
+    h = __uint_as_float((neg ? 0x80000000u : 0u) | ((unsigned int)(eh + 127) << 23) | (keep & 0x7fffffu));
+    if (neg) diff = -diff;
+    c = __int2float_rn(diff) * __uint_as_float((unsigned int)(e - 52 + 127) << 23);  // exact scaling by 2^(e - 52)
+}
+
 template <>
 __device__ __forceinline__ void store_tau<float>(float *tau, float *tau_c, int64_t i, double x)
 {
-    const float h = __double2float_rn(x);
+    float h, c;
+    split_f32_pair(x, h, c);
     tau[i] = h;
-    tau_c[i] = __double2float_rn((double)h - x);
+    tau_c[i] = c;
 }
 
 // -ln U in FP64 for U in [2^-54, 1]: Tang's logarithm (within 2 ulp); above
@@ -298,19 +333,24 @@ __device__ __forceinline__ void store_tau<float>(float *tau, float *tau_c, int64
 // remainder d^8/8 is below 2^-59 of the result.  The optical-depth resets are
 // the event kernels' largest FP64 cost, and GB300's FP64 pipe their bound when
 // many particles fire.
+static __device__ __noinline__ double neg_log1p_series(double u)
+{
+    const double d = u - 1.0;
+    double q = fma(d, -1.0 / 7, 1.0 / 6);
+    q = fma(d, q, -0.2);
+    q = fma(d, q, 0.25);
+    q = fma(d, q, -1.0 / 3);
+    q = fma(d, q, 0.5);
+    return fma(d * d, q, -d);  // -(d - d^2/2 + d^3/3 - ... - d^7/7)
+}
+
 __device__ __forceinline__ double neg_log_u(double u)
 {
     // (positive doubles order as their bit patterns: the test costs no FP64
-    // instruction, and U >= 2^-54 is normal, so Tang's core needs no range check)
-    if (__double_as_longlong(u) > __double_as_longlong(1.0 - 0x1p-8)) {
-        const double d = u - 1.0;
-        double q = fma(d, -1.0 / 7, 1.0 / 6);
-        q = fma(d, q, -0.2);
-        q = fma(d, q, 0.25);
-        q = fma(d, q, -1.0 / 3);
-        q = fma(d, q, 0.5);
-        return fma(d * d, q, -d);  // -(d - d^2/2 + d^3/3 - ... - d^7/7)
-    }
+    // instruction; the series is out of line, so that the other 99.6 % of the
+    // draws do not issue it predicated off; U >= 2^-54 is normal, so Tang's core
+    // needs no range check)
+    if (__double_as_longlong(u) > __double_as_longlong(1.0 - 0x1p-8)) return neg_log1p_series(u);
     return -log_tang_core(u, 0);
 }
 
