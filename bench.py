@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-schwinger", action="store_true")
     ap.add_argument("--no-longrun", action="store_true")
     ap.add_argument("--no-paper-table", action="store_true")
+    ap.add_argument("--paper-table-n", type=int, default=100_000_000,
+                    help="particles of the per-kernel table leg (the paper's tables use 1e8)")
     ap.add_argument("--cascade-scale", type=float, default=1.0,
                     help="fraction of the 64 patch counts round(10^(3+4U)) to run in the cascade leg")
     ap.add_argument("--cascade-steps", type=int, default=2000)
@@ -998,7 +1000,7 @@ def gpu_main(args):
         result.setdefault("paths", {})["fp32_mlp"] = mlp_leg(api, tabs, bufs, fire, args, ws)
 
     if not args.no_paper_table:
-        result["paper_table"] = paper_table_leg(api, tabs)
+        result["paper_table"] = paper_table_leg(api, tabs, n=args.paper_table_n)
 
     if not args.no_cascade:
         del bufs, fire
