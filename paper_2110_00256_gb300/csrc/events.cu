@@ -3,6 +3,8 @@
 // production (§2.1, §3.1), one kernel for the three lists of a substep, and the
 // fused three-species substep entry point.
 // The per-warp routines are in events.cuh (shared with the batched kernels).
+#include <cmath>
+
 #include "events.cuh"
 #include "evolve.cuh"
 
@@ -142,6 +144,8 @@ EventCommon<T> event_common(const qed_tables *t, int proc, uint64_t seed, int64_
     c.step = step;
     c.d_step = o ? o->d_step : nullptr;
     c.threshold = o ? o->photon_threshold : 0.0;
+    c.threshold_f = (float)c.threshold;
+    if ((double)c.threshold_f < c.threshold) c.threshold_f = std::nextafter(c.threshold_f, INFINITY);
     c.stats = o ? (long long *)o->d_stats : nullptr;
     c.copy_fields = 1;
     if (o && o->sampler == 1) c.mlpv = mlp_view((const qed_mlp *)o->mlp, proc);

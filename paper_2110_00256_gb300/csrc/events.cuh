@@ -56,6 +56,7 @@ struct EventCommon {
     int64_t step;
     const int64_t *d_step;    // if set, the step is read from here
     double threshold;
+    float threshold_f;        // the smallest float >= threshold: gg >= threshold_f iff (double)gg >= threshold
     long long *stats;
     int copy_fields;          // 0: products get no field values (the caller computes them, see qed_push_substep_batched)
 };
@@ -140,7 +141,9 @@ __device__ __forceinline__ void qs_event_chunk(const EventSeg<T> &g, const Event
     const T inv = pm > T(0) ? T(1) / pm : T(0);
     const T nx = px * inv, ny = py * inv, nz = pz * inv;
 
-    const bool keep = valid && (double)gg >= c.threshold;
+    // (the FP32 test against the float threshold decides as the FP64 one does,
+    // without FP64 instructions)
+    const bool keep = valid && (sizeof(T) == 4 ? (float)gg >= c.threshold_f : (double)gg >= c.threshold);
     const long long slot = warp_reserve(G.count, keep);
     const bool room = !keep || slot < G.cap;
     const bool exec = valid && room;

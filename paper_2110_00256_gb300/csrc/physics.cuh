@@ -168,8 +168,28 @@ template <typename T>
 __device__ __forceinline__ T sample_uniform(double u);
 template <>
 __device__ __forceinline__ double sample_uniform<double>(double u) { return u; }
+// FP32: u rounded toward zero, from the bits (u >= 2^-54 is a normal float;
+// the same value as __double2float_rz without an FP64 instruction)
 template <>
-__device__ __forceinline__ float sample_uniform<float>(double u) { return __double2float_rz(u); }
+__device__ __forceinline__ float sample_uniform<float>(double u)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    return __uint_as_float((unsigned int)((((b >> 52) & 0x7ffu) - 1023u + 127u) << 23) |
+                           (unsigned int)((b >> 29) & 0x7fffffu));
+}
+
+// 1 - u rounded toward zero to FP32 for a draw u in [1/2, 1] (the BW fold):
+// 1 - u = (2^53 - M) 2^-53 exactly, M the 53-bit significand of u, then the
+// top 24 bits of that integer
+__device__ __forceinline__ float one_minus_rz(double u)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    if (b >= 0x3ff0000000000000ull) return 0.0f;                        // u = 1
+    const unsigned long long n = (1ull << 53) - ((b & 0xfffffffffffffull) | (1ull << 52));  // u in [1/2, 1)
+    const int len = 64 - __clzll((long long)n);                          // 1 .. 52
+    const unsigned int mant = (unsigned int)(len > 24 ? n >> (len - 24) : n << (24 - len)) & 0x7fffffu;
+    return __uint_as_float(((unsigned int)(len - 1 - 53 + 127) << 23) | mant);
+}
 
 // interpolated row value of a 2-D table at column m: v_n,m + w (v_{n+1},m - v_n,m)
 template <typename T>
@@ -257,8 +277,12 @@ template <typename T>
 __device__ __forceinline__ T bw_sample_xi(const Table2D<T> &tb, T chi, double u, bool &electron)
 {
     // split on the FP64 draw, then round the folded value (keeps 1 - u accurate)
-    electron = u <= 0.5;
-    const T r = sample_uniform<T>(electron ? u : 1.0 - u);
+    electron = __double_as_longlong(u) <= __double_as_longlong(0.5);  // u <= 1/2 (u > 0: the bits order as the values)
+    T r;
+    if constexpr (sizeof(T) == 4)
+        r = electron ? sample_uniform<T>(u) : one_minus_rz(u);
+    else
+        r = electron ? u : 1.0 - u;
     const T *r0, *r1;
     T w;
     size_t off;

@@ -168,6 +168,38 @@ def test_init_optical_depth_matches_oracle(api, prec_name):
     assert np.allclose(got, ref, rtol=1e-14 if prec_name == "f64" else 1e-13, atol=0)
 
 
+@pytest.mark.parametrize("prec_name", ["f64", "f32"])
+def test_init_optical_depth_extreme_draws(api, prec_name):
+    """-ln U at the ends of the draw (§3): ids picked on the host (by the
+    oracle's own draws among 2e7) whose U lies within 1e-6 of 1 (the optical
+    depth ~1e-8 .. 1e-6, where the kernels take the Taylor series of log1p(U - 1)
+    instead of the table-driven logarithm), around the switch at U = 1 - 2^-8,
+    and below 3e-7 (optical depths above 15), with ordinary ones beside them;
+    the GPU's optical depths equal the oracle's to 1e-14 relative (FP64) and
+    1e-13 (the FP32 path's float pair)."""
+    prec = api.QED_F64 if prec_name == "f64" else api.QED_F32
+    seed, step = 987654321, 3
+    cand = np.arange(20_000_000, dtype=np.uint64)
+    tau_c = oracle.init_tau(cand, seed, step)
+    near_one = cand[tau_c < 1e-6]
+    switch = cand[np.abs(tau_c - 2.0 ** -8) < 2e-5][:500]
+    series = cand[(tau_c < 2.0 ** -8) & (tau_c >= 1e-6)][:2000]
+    tail = cand[tau_c > 15.0]
+    ordinary = cand[:5000]
+    ids = np.concatenate([near_one, switch, series, tail, ordinary])
+    assert len(near_one) >= 5 and len(tail) >= 5 and len(switch) >= 100
+    sp = api.SpeciesBuffers(len(ids), prec)
+    sp.arrays["id"].copy_(torch.as_tensor(ids.view(np.int64)))
+    sp.count.fill_(len(ids))
+    api.qed_init_optical_depth(sp, seed=seed, step=step)
+    torch.cuda.synchronize()
+    got = tau_eff(sp.to_host(), prec == api.QED_F32)
+    ref = oracle.init_tau(ids, seed, step)
+    rel = np.abs(got - ref) / ref
+    print(f"{prec_name}: smallest tau {ref.min():.3e}, largest {ref.max():.2f}, worst relative error {rel.max():.2e}")
+    assert np.all(rel <= (1e-14 if prec_name == "f64" else 1e-13)), (ids[np.argmax(rel)], rel.max())
+
+
 def test_bw_asymptotes_against_oracle(api):
     """Breit-Wheeler rates below and above a narrow table (chi in [1, 10]) come
     from the asymptotes of T (Eq. (t_func)); each photon's |p| is chosen so that
