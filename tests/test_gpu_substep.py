@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import (FIELDS, as_f64, check_substep_fp32, compare_states as _compare, gpu_tables,
+from helpers import (FIELDS, as_f64, check_substep_by_event, compare_states as _compare, gpu_tables,
                      margin_ids as _margin_ids, sort_by_id, tau_bound, tau_eff)
 
 torch = pytest.importorskip("torch")
@@ -97,10 +97,35 @@ def test_substep_fp32_parity(api, tabs):
     h32 = {k: as_f64(v, np.float32) for k, v in host.items()}
     got, st, fire = _run_gpu(api, t, host, api.QED_F32, dt=10.0, seed=7, step=1)
     fl = {k: (f.idx[:f.n()].cpu().numpy(), f.chi[:f.n()].cpu().numpy()) for k, f in zip(SPECIES, fire)}
-    rep = check_substep_fp32(ot, h32, got, fl, 10.0, 7, 1)
+    rep = check_substep_by_event(ot, h32, got, fl, 10.0, 7, 1)
     assert rep["events"] > 200
     assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0
     print("fp32 substep:", rep)
+
+
+@pytest.mark.parametrize("prec_name", ["f64", "f32"])
+def test_substep_every_particle_fires(api, tabs, prec_name):
+    """Optical depths of order 1e-12, so that nearly every particle fires (as
+    in the paper's per-kernel benchmark of emission and pair production): 4e4
+    emissions and 2e4 pair productions in one step, checked event by event
+    against the oracle: the chi of the firing list, every sample by its backward
+    error at the GPU's chi, energy and direction of the products, the optical
+    depths drawn for parents and children, fields and weights copied.  (With
+    every particle firing, the small-chi ones included, the FP64 chi of many
+    events differ from the oracle's within the cancellation bound of a
+    difference of squares, and a sampled xi inherits that; a forward
+    comparison of the products would measure the chi, not the sampling.)"""
+    ot, t = tabs
+    host = _inputs(20_000, 41, tau_scale=1e-12)
+    prec = api.QED_F64 if prec_name == "f64" else api.QED_F32
+    hp = {k: as_f64(v, np.float64 if prec_name == "f64" else np.float32) for k, v in host.items()}
+    got, st, fire = _run_gpu(api, t, host, prec, dt=10.0, seed=5, step=2, extra=4.0)
+    fl = {k: (f.idx[:f.n()].cpu().numpy(), f.chi[:f.n()].cpu().numpy()) for k, f in zip(SPECIES, fire)}
+    rep = check_substep_by_event(ot, hp, got, fl, 10.0, 5, 2, fp64=prec_name == "f64")
+    print(f"{prec_name} all-fire substep:", rep)
+    assert rep["events"] > 55_000
+    assert st["qs_events"] > 35_000 and st["pairs"] > 15_000
+    assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0
 
 
 def test_energy_conservation_and_threshold(api, tabs):
