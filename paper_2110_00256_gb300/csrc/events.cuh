@@ -132,13 +132,18 @@ __device__ __forceinline__ void qs_event_chunk(const EventSeg<T> &g, const Event
     }
 
     const T p2 = px * px + py * py + pz * pz;
-    const T pm = d_sqrt(p2);
+    T inv;  // 1/|p|
+    if constexpr (sizeof(T) == 8) {
+        inv = p2 > T(0) ? rsqrt(p2) : T(0);  // (within 1 ulp; no FP64 division)
+    } else {
+        const T pm = d_sqrt(p2);
+        inv = pm > T(0) ? T(1) / pm : T(0);
+    }
     const T gamma = d_sqrt(T(1) + p2);
     const T gg = (gamma - T(1)) * xi;  // photon energy (§2.2)
     const T g1 = gamma - gg;            // lepton energy after emission
     const T q = (g1 - T(1)) * (g1 + T(1));
     const T pn = d_sqrt(q > T(0) ? q : T(0));
-    const T inv = pm > T(0) ? T(1) / pm : T(0);
     const T nx = px * inv, ny = py * inv, nz = pz * inv;
 
     // (the FP32 test against the float threshold decides as the FP64 one does,
@@ -198,9 +203,14 @@ __device__ __forceinline__ void bw_event_chunk(const EventSeg<T> &g, const Event
         xp = electron ? T(1) - xs : xs;
     }
 
-    const T gg = d_sqrt(px * px + py * py + pz * pz);  // photon energy
-    const bool pair = valid && gg > T(2);                // below 2 m_e c^2 no pair
-    const T inv = gg > T(0) ? T(1) / gg : T(0);
+    const T p2 = px * px + py * py + pz * pz;
+    const T gg = d_sqrt(p2);  // photon energy (IEEE: it decides whether a pair is made, as in the oracle)
+    T inv;
+    if constexpr (sizeof(T) == 8)
+        inv = p2 > T(0) ? rsqrt(p2) : T(0);  // (within 1 ulp; no FP64 division)
+    else
+        inv = gg > T(0) ? T(1) / gg : T(0);
+    const bool pair = valid && gg > T(2);  // below 2 m_e c^2 no pair
     const T nx = px * inv, ny = py * inv, nz = pz * inv;
     const T km = (gg - T(2)) * xm, kp = (gg - T(2)) * xp;  // kinetic energies (§2.1)
     const T pmm = d_sqrt(km * (km + T(2))), pmp = d_sqrt(kp * (kp + T(2)));
