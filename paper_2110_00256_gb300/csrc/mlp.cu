@@ -53,7 +53,10 @@ __global__ void mlp_to_bf16_kernel(const float *p, __nv_bfloat16 *w)
 // ---------------------------------------------------------------------------
 // training: one CTA of kTrainThreads threads takes kTrainThreads samples at a
 // time (one per thread) and accumulates the gradient of the mean squared error
-// in shared memory; one atomic flush per CTA at the end.
+// in shared memory; each CTA stores its sums (gradient and loss) in a slot of
+// its own, and mlp_reduce_kernel adds the slots in CTA order, so that a
+// training run gives the same bits every time (atomic adds across CTAs would
+// round in the order the CTAs arrive).
 // ---------------------------------------------------------------------------
 constexpr int kTrainThreads = 128;
 constexpr int kTS = kTrainThreads + 1;  // padded sample stride of the [64][samples] buffers
@@ -68,7 +71,6 @@ struct TrainSmem {
     float z2[kMlpH * kTS];     // z2, then d2 = dL/dz2
     float q[kMlpH * kTS];      // dy * h2, then d1 = dL/dz1
     float x[2][kTrainThreads], dy[kTrainThreads];
-    float loss;
 };
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -76,7 +78,7 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, const double *__restrict__ chi,
                                                                     const double *__restrict__ uu,
                                                                     const double *__restrict__ xi, int64_t n,
-                                                                    float *grad, float *loss_out)
+                                                                    float *part)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
@@ -92,10 +94,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
         S.w3[i] = __bfloat162float(v.w[kOffW3 + i]);
     }
     for (int i = tid; i < kMlpParams; i += blockDim.x) S.g[i] = 0.f;
-    if (tid == 0) {
-        S.b3 = __bfloat162float(v.w[kOffB3]);
-        S.loss = 0.f;
-    }
+    if (tid == 0) S.b3 = __bfloat162float(v.w[kOffB3]);
     __syncthreads();
     const float inv_n = 1.0f / (float)n;
     float my_loss = 0.f;
@@ -187,10 +186,29 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(MlpView v, con
         }
         __syncthreads();
     }
-    atomicAdd(&S.loss, my_loss);
+    S.dy[tid] = my_loss;  // (the per-sample buffer is free after the last pass)
     __syncthreads();
-    for (int i = tid; i < kMlpParams; i += blockDim.x) atomicAdd(grad + i, S.g[i]);
-    if (tid == 0) atomicAdd(loss_out, S.loss * inv_n);
+    float *slot = part + (size_t)blockIdx.x * (kMlpParams + 1);
+    for (int i = tid; i < kMlpParams; i += blockDim.x) slot[i] = S.g[i];
+    if (tid == 0) {
+        float l = 0.f;
+        for (int s = 0; s < kTrainThreads; ++s) l += S.dy[s];
+        slot[kMlpParams] = l * inv_n;
+    }
+}
+
+// the training kernel's per-CTA slots summed in CTA order: the gradient, and
+// the batch's mean loss into loss_out
+__global__ void mlp_reduce_kernel(const float *__restrict__ part, int slots, float *grad, float *loss_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kMlpParams) return;
+    float a = 0.f;
+    for (int c = 0; c < slots; ++c) a += part[(size_t)c * (kMlpParams + 1) + i];
+    if (i < kMlpParams)
+        grad[i] = a;
+    else
+        *loss_out = a;
 }
 
 // Adam (Kingma & Ba 2015); refreshes the bf16 copy and clears the gradient
@@ -512,7 +530,7 @@ static void free_mlp(qed_mlp *m)
 {
     if (!m) return;
     for (int p = 0; p < 2; ++p) {
-        void *ptrs[] = {m->master[p], m->adam_m[p], m->adam_v[p], m->grad[p], m->loss[p], m->w[p]};
+        void *ptrs[] = {m->master[p], m->adam_m[p], m->adam_v[p], m->grad[p], m->part[p], m->loss[p], m->w[p]};
         for (void *x : ptrs)
             if (x) cudaFree(x);
     }
@@ -527,12 +545,15 @@ static qed_status create_mlp(const double chi_min[2], const double chi_max[2], u
     memset(m, 0, sizeof(*m));
     cudaGetDevice(&m->device);
     for (int p = 0; p < 2; ++p) m->chi_min[p] = chi_min[p], m->chi_max[p] = chi_max[p];
+    m->part_slots = sm_count();
     for (int p = 0; p < 2; ++p) {
         cudaError_t e = cudaSuccess;
         float **fp[] = {&m->master[p], &m->adam_m[p], &m->adam_v[p], &m->grad[p]};
         for (float **f : fp)
             if (e == cudaSuccess) e = cudaMalloc((void **)f, kMlpParams * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void **)&m->loss[p], sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&m->part[p], (size_t)m->part_slots * (kMlpParams + 1) * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void **)&m->w[p], kMlpParams * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_m[p], 0, kMlpParams * sizeof(float), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_v[p], 0, kMlpParams * sizeof(float), st);
@@ -688,12 +709,13 @@ static qed_status launch_train(qed_mlp *m, int proc, const double *chi, const do
         QED_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    QED_CUDA_TRY(cudaMemsetAsync(m->loss[proc], 0, sizeof(float), st));
     int64_t blocks = (n + kTrainThreads - 1) / kTrainThreads;
-    const int64_t cap = (int64_t)sm_count();
+    const int64_t cap = (int64_t)m->part_slots;
     blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
-    mlp_train_kernel<<<(int)blocks, kTrainThreads, sm, st>>>(mlp_view(m, proc), chi, u, xi, n, m->grad[proc],
-                                                             m->loss[proc]);
+    mlp_train_kernel<<<(int)blocks, kTrainThreads, sm, st>>>(mlp_view(m, proc), chi, u, xi, n, m->part[proc]);
+    QED_LAUNCH_CHECK();
+    mlp_reduce_kernel<<<(kMlpParams + 1 + 255) / 256, 256, 0, st>>>(m->part[proc], (int)blocks, m->grad[proc],
+                                                                   m->loss[proc]);
     QED_LAUNCH_CHECK();
     return QED_OK;
 }

@@ -334,6 +334,8 @@ struct qed_mlp {
     float *master[2];         // FP32 master parameters
     float *adam_m[2], *adam_v[2];
     float *grad[2];           // gradient accumulator (FP32)
+    float *part[2];           // per-CTA gradients and loss of the training kernel, [slot][kMlpParams + 1]
+    int part_slots;           // CTAs the training kernel may use (one slot each)
     float *loss[2];           // accumulated loss of the last batch
     __nv_bfloat16 *w[2];      // bf16 parameters used by every forward pass
     int64_t step[2];          // Adam step count

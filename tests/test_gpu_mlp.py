@@ -152,6 +152,25 @@ def test_gradients_match_oracle(api, tables, proc):
         assert rel < 2e-2, (name, rel)
 
 
+def test_training_is_deterministic(api, tables):
+    """Two networks from the same seed trained on the same batches end with the
+    same parameters bit for bit (the training kernel's per-CTA gradient sums
+    are added in CTA order, not by atomics), and so do their losses."""
+    from paper_2110_00256_gb300 import surrogate
+    chi, u, xi = surrogate.make_data(tables, 1, 200_000, seed=4, rows=2000)
+    runs = []
+    for _ in range(2):
+        m = api.Mlp(tables, seed=9)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        hist = []
+        for b in range(0, 200_000, 4096):
+            m.train_step(1, chi[b:b + 4096], u[b:b + 4096], xi[b:b + 4096], 3e-3, loss)
+            hist.append(float(loss.item()))
+        runs.append((m.get_params(1), np.array(hist)))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][1][-1] < runs[0][1][0]  # and it learns
+
+
 def test_substep_with_learned_sampler(api, tables):
     from paper_2110_00256_gb300 import workloads
     m = api.Mlp(tables, seed=41)

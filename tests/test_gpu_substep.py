@@ -128,6 +128,41 @@ def test_substep_every_particle_fires(api, tabs, prec_name):
     assert st["dropped_capacity"] == 0 and st["nonfinite"] == 0
 
 
+def test_substep_fp64_config1_with_events(api):
+    """The 10^4-electron FP64 case (static B = 0.01 along z, gamma = 10^(2 + 2U),
+    isotropic, 64-point tables) with dt = 10 instead of 1e-3, so that photons
+    are emitted (~370 emissions over the 100 steps; the photons' chi stays far
+    below pair production's): every step of the whole substep against the
+    oracle run from the GPU's own pre-step state (decisions within the error
+    bound excluded)."""
+    from paper_2110_00256_gb300 import workloads
+    ot = oracle.tables(qs_n_chi=64, qs_n_xi=64, bw_n_chi=64, bw_n_xi=64)
+    t = gpu_tables(api, ot)
+    beam = workloads.isotropic_beam(10_000, 0)
+    empty = {k: v[:0] for k, v in beam.items()}
+    bufs = {"electrons": api.SpeciesBuffers(20_000, api.QED_F64).set(beam),
+            "positrons": api.SpeciesBuffers(10_000, api.QED_F64),
+            "photons": api.SpeciesBuffers(20_000, api.QED_F64)}
+    fire = [api.FireBuffers(20_000) for _ in SPECIES]
+    events = 0
+    for step in range(100):
+        pre = {k: bufs[k].to_host() for k in SPECIES}
+        pre = {k: {kk: (v.astype(np.uint64) if kk == "id" else v) for kk, v in pre[k].items()
+                   if kk in empty} for k in SPECIES}
+        stats = api.Stats()
+        api.qed_substep(t, bufs["electrons"], bufs["positrons"], bufs["photons"], 10.0, 11, step, fire,
+                        stats=stats)
+        torch.cuda.synchronize()
+        ref = oracle.substep(ot, pre, dt=10.0, seed=11, step=step)
+        got = {k: bufs[k].to_host() for k in SPECIES}
+        excl = _margin_ids(ot, pre, 10.0, 1e-12, 11, step)
+        _compare(got, ref, False, 1e-12, exclude=excl)
+        st = stats.as_dict()
+        events += st["qs_events"] + st["bw_events"]
+    print("config-1 beam with dt = 10: events over 100 steps", events)
+    assert events > 100
+
+
 def test_energy_conservation_and_threshold(api, tabs):
     ot, t = tabs
     host = _inputs(50_000, 31)
