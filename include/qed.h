@@ -504,7 +504,9 @@ qed_status qed_mlp_set_params(qed_mlp *m, qed_process proc, const float *host_pa
  * of a batch: device arrays chi[n], u[n], xi[n] (FP64; for BW xi is the
  * electron's fraction chi_-/chi_g).  d_loss (device float, may be NULL)
  * receives the batch loss before the step.  Calls on one network must not
- * overlap. */
+ * overlap.  Deterministic: the same network and batches give the same
+ * parameters bit for bit (the per-CTA gradient sums are added in a fixed
+ * order). */
 qed_status qed_mlp_train_step(qed_mlp *m, qed_process proc, const double *d_chi, const double *d_u,
                               const double *d_xi, int64_t n, float lr, float *d_loss, void *stream);
 /* Gradient of the batch loss with respect to the parameter vector (device
