@@ -13,11 +13,13 @@ defines it:
   layer 2    h2 = gelu(W2 bf16(h1) + b2)       (64), bf16 = round to bfloat16
   layer 3    y  = W3 . h2 + b3
   output     QS: ln(xi / (1 - xi)) = y + 3 ln U + L(chi_c),  L(chi) = ln(chi / (1 + chi))
-             BW: xi_s = clamp(1/2 - w(chi_c) y, 0, 1/2),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
+             BW: xi_s = min(1/2, 1 / (1 + exp(4 w(chi_c) y))),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
              (xi_s is the electron's fraction if U <= 1/2, else the positron's;
              L and w centre and scale y: xi ~ U^3 as U -> 0 and grows with chi,
-             the logit resolves 1 - xi at the hard end, and the pair split
-             narrows around 1/2 with width ~ sqrt(3 chi / 64))
+             the logit resolves 1 - xi at the hard end; the pair split narrows
+             around 1/2 with width ~ sqrt(3 chi / 64) for small chi, where the
+             BW map is 1/2 - w y to first order, and at large chi the folded
+             split crowds towards 0, which its logit resolves)
   gelu(x)    = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))   (Hendrycks & Gimpel)
   loss       mean over the batch of (y - t)^2, with t the y whose output is xi*,
              xi* the reference sample of the same (chi, U)
@@ -110,7 +112,8 @@ def targets(proc: int, chi, u, xi, chi_min, chi_max):
     if proc == 0:
         return np.log(xi) - np.log1p(-xi) - 3.0 * np.log(u) - cs
     xs = np.where(u <= 0.5, xi, 1.0 - xi)  # folded fraction of the sampled lepton, in [0, 1/2]
-    return (0.5 - xs) / cs
+    xs = np.clip(xs, 1e-300, 0.5)
+    return np.log((1.0 - xs) / xs) / (4.0 * cs)
 
 
 def loss_and_grad(theta, X, t, round_bf16=True):
@@ -139,7 +142,7 @@ def output(proc: int, y, chi, u, chi_min, chi_max):
     cs = centre_scale(proc, chi, chi_min, chi_max)
     if proc == 0:
         return 1.0 / (1.0 + np.exp(-(y + 3.0 * np.log(u) + cs)))
-    return np.clip(0.5 - cs * np.asarray(y, dtype=np.float64), 0.0, 0.5)
+    return np.minimum(0.5, 1.0 / (1.0 + np.exp(4.0 * cs * np.asarray(y, dtype=np.float64))))
 
 
 def adam(theta, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -11,9 +11,10 @@
 //       (xi ~ U^3 as U -> 0, xi scales with chi for small chi, and the logit
 //       resolves the hard end xi -> 1 in 1 - xi);
 //   BW: the folded fraction of the lepton U selects (U <= 1/2: the electron)
-//       xi_s = clamp(1/2 - w(chi_c) y, 0, 1/2),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
-//       (the pair split concentrates around 1/2 with a width ~ sqrt(3 chi / 64)
-//       for small chi).
+//       xi_s = min(1/2, 1 / (1 + exp(4 w(chi_c) y))),  w(chi) = sqrt(chi / (chi + 16/3)) / 2
+//       (for small chi the pair split concentrates around 1/2 with a width
+//       ~ sqrt(3 chi / 64), where the map is 1/2 - w y to first order; for large
+//       chi the folded split crowds towards 0, which the logit resolves).
 // Activation: GELU in its tanh form, the FP32 arithmetic in packed pairs
 // (f32x2) and tanh.approx.f32 (~2^-11), the same instructions in training and
 // in every inference path.
@@ -166,17 +167,18 @@ __device__ __forceinline__ double mlp_output(int proc, float y, const MlpIn &in)
         const float l = fmaf(3.0f, in.lnu, y + in.base);
         return (double)(1.0f / (1.0f + __expf(-l)));
     }
-    float xs = fmaf(-in.base, y, 0.5f);
-    xs = xs < 0.0f ? 0.0f : (xs > 0.5f ? 0.5f : xs);
-    return (double)(in.low ? xs : 1.0f - xs);
+    float xs = 1.0f / (1.0f + __expf(4.0f * in.base * y));
+    xs = xs > 0.5f ? 0.5f : xs;  // (a NaN y stays NaN)
+    return in.low ? (double)xs : 1.0 - (double)xs;  // (1 - xs in FP64 keeps a small xs)
 }
 
 // the output y whose map gives xi (the training target of a sample)
 __device__ __forceinline__ float mlp_target(int proc, double xi, const MlpIn &in)
 {
     if (proc == QED_PROC_QS) return (float)(log(xi) - log1p(-xi)) - fmaf(3.0f, in.lnu, in.base);
-    const float xs = (float)(in.low ? xi : 1.0 - xi);
-    return (0.5f - xs) / in.base;
+    double xs = in.low ? xi : 1.0 - xi;
+    xs = xs < 1e-300 ? 1e-300 : (xs > 0.5 ? 0.5 : xs);
+    return (float)((log1p(-xs) - log(xs)) / (4.0 * (double)in.base));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)

@@ -62,12 +62,11 @@ def _y_of(proc, xi, chi, u, y_ref, cmin, cmax):
     """The network output that the GPU's xi implies (the inverse of the output
     map), and where the map is not clamped by the reference output."""
     y_gpu = omlp.targets(proc, chi, u, xi, cmin, cmax)
-    cs = omlp.centre_scale(proc, chi, cmin, cmax)
     if proc == 0:
         ok = (xi > 1e-30) & (xi < 1 - 1e-5)  # where the FP32 output keeps 1 - xi to 1e-2 or better
     else:
-        xs = 0.5 - cs * y_ref
-        ok = (xs > 1e-3) & (xs < 0.5 - 1e-3)
+        xs = omlp.output(1, y_ref, chi, u, cmin, cmax)
+        ok = (xs > 1e-6) & (xs < 0.5 - 1e-3)
     return y_gpu, ok
 
 

@@ -80,11 +80,21 @@ def test_output_maps():
     bw = mlp.output(1, yb, chib, u, 0.02, 1e3)
     wb = 0.5 * np.sqrt(chib / (chib + 16.0 / 3.0))
     assert wb[2] == pytest.approx(0.5 / math.sqrt(2.0))
-    assert np.allclose(bw, np.clip(0.5 - wb * yb, 0.0, 0.5)) and bw[2] == 0.5 and bw[3] == 0.0
-    # targets take the electron's fraction and fold it by U
+    # the logit of the folded split is 4 w y; y < 0 clamps at 1/2
+    assert bw[2] == 0.5 and np.all(bw <= 0.5)
+    k = [0, 1, 3]
+    assert np.allclose(np.log((1 - bw[k]) / bw[k]), 4 * wb[k] * yb[k], rtol=1e-12)
+    # near 1/2 the map is 1/2 - w y to first order (the linear map of a narrow split)
+    eps = 1e-4
+    near = mlp.output(1, np.array([eps]), np.array([0.1]), np.array([0.3]), 0.02, 1e3)[0]
+    w01 = 0.5 * math.sqrt(0.1 / (0.1 + 16.0 / 3.0))
+    assert abs(near - (0.5 - w01 * eps)) < 1e-3 * w01 * eps
+    # at large chi it resolves the crowded small splits: y = ln((1 - xi_s) / xi_s) / (4 w)
+    assert bw[3] == pytest.approx(1.0 / (1.0 + math.exp(4 * wb[3] * 3.0)), rel=1e-12) and bw[3] < 3e-3
+    # targets take the electron's fraction and fold it by U, and invert the map
     xe = np.where(u <= 0.5, bw, 1 - bw)
     tb = mlp.targets(1, chib, u, xe, 0.02, 1e3)
-    assert np.allclose(tb[:2], yb[:2])
+    assert np.allclose(tb[k], yb[k], rtol=1e-9) and tb[2] == 0.0
     X = mlp.features(1, [1e-5, 1.0, 1e9], [0.2, 0.9, 0.5], 0.02, 1e3)
     assert X[0, 0] == -1.0 and X[2, 0] == 1.0
     assert np.allclose(X[:, 1], [2 * 0.4 - 1, 2 * 0.2 - 1, 1.0])
