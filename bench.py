@@ -304,7 +304,7 @@ def mlp_leg(api, tabs, bufs, fire, args, ws):
     r = time_substep(api, tabs, bufs, fire, k, 2, ws, step0=1000, mlp=mlp)
     ms = max_over_ranks(ws, r["ms"])
     out = {"value": sum_over_ranks(ws, r["n_before"] * k) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k,
-           "train_s": round(train_s, 2), "train_samples_per_process": 10_000_000, "train_epochs": 48,
+           "train_s": round(train_s, 2), "train_samples_per_process": 10_000_000, "train_epochs": {"0": 48, "1": 96},
            "train_batch": 4096, "exact_targets_s": {p: round(train[p]["data_seconds"], 2) for p in train},
            "train_final_loss": {p: round(train[p]["final_loss"], 6) for p in train}}
     n = 100_000_000

@@ -42,14 +42,17 @@ def make_data(tables: api.Tables, proc: int, n: int, seed: int, rows: int = 1638
     return chi[perm], u[perm], xi[perm]
 
 
-def train(mlp: api.Mlp, data_tables: api.Tables, proc: int, n_samples: int = 10_000_000, epochs: int = 48,
+def train(mlp: api.Mlp, data_tables: api.Tables, proc: int, n_samples: int = 10_000_000, epochs: int | None = None,
           batch: int = 4096, lr: float = 4e-3, lr_final: float = 1e-4, seed: int = 1, log_every: int = 0):
     """Train one network on n_samples exact samples (epochs passes, Adam with a
     cosine decay of the step size from lr to lr_final); returns the loss history
-    (one value per logged step) and timings.  The defaults (1.2e5 steps of 4096
-    samples) put the worst chi bin's KS distance to the exact distribution near
-    1e-3 for both processes; 8 epochs of 16384 (5e3 steps) left the pair-split
-    network's near 7e-3: the accuracy follows the number of steps."""
+    (one value per logged step) and timings.  The defaults, 48 epochs of 4096
+    (1.2e5 steps) for photon emission and 96 (2.3e5 steps) for the pair split,
+    put every chi bin's KS distance to the exact distribution below 1e-3; 8
+    epochs of 16384 (5e3 steps) had left the pair-split network's worst bin
+    near 7e-3: the accuracy follows the number of steps."""
+    if epochs is None:
+        epochs = 48 if proc == api.QED_PROC_QS else 96
     t_data = time.perf_counter()
     chi, u, xi = make_data(data_tables, proc, n_samples, seed)
     n_samples = chi.numel()  # (a whole number of draws per chi value)
